@@ -1,0 +1,221 @@
+/*
+ * qt.h -- C ABI of the GB300 (sm_103a) quantum-trajectory library.
+ *
+ * Method: "Simulations of Quantum Circuits with Approximate Noise using qsim
+ * and Cirq" (arXiv 2111.02396).  A noisy circuit (gates and noise channels,
+ * Sec. II) is simulated by quantum trajectories (Sec. III.E): one Kraus
+ * operator is sampled per channel and applied to a 2^n-amplitude complex64
+ * state vector; gates are fused (Sec. III.B) and applied as 2^q x 2^q
+ * matrix-vector products over the state (Alg. 1); branch probabilities are
+ * evaluated only when the lower bounds do not decide (delayed inner products,
+ * Alg. 2).
+ *
+ * Conventions
+ *   - amplitude index bit j is qubit j; an operator on qubits Q[0..q-1] is a
+ *     2^q x 2^q row-major matrix whose index bit b is qubit Q[b];
+ *   - matrices cross the ABI as interleaved (re, im) FP64;
+ *   - every trajectory starts in |0...0>;
+ *   - random numbers: Philox4x32-10 (Salmon et al., SC'11), key = seed,
+ *     counter = (traj_lo, traj_hi, stream, index); stream 0 index c draws
+ *     the uniform of channel c (circuit order), stream 1 index j draws the
+ *     uniform of sample j; u01 = ((w0 >> 5) * 2^26 + (w1 >> 6)) * 2^-53.
+ *
+ * Errors: every call returns a qt_status; 0 is success, negative values are
+ * errors and leave outputs unspecified.  No call aborts the process.  The
+ * message of the last error on the calling thread is qt_last_error().
+ *
+ * Ownership: handles (qt_circuit, qt_fused, qt_run, qt_server) are owned by
+ * the library and freed by their *_destroy call; arrays passed in are read
+ * during the call only (copied where kept); output arrays are owned by the
+ * caller and sized as each call states.  Device memory comes from the
+ * allocator installed with qt_set_allocator (stream-ordered cudaMallocAsync
+ * by default).  qt_circuit and qt_fused handles are immutable after
+ * creation and may be shared between threads; a qt_run is used by one
+ * thread at a time.
+ */
+#ifndef QT_H
+#define QT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QT_OK = 0,
+  QT_ERR_INVALID_ARG = -1,   /* malformed input (range, moment overlap, sizes) */
+  QT_ERR_NOT_CPTP = -2,      /* Kraus list with sum K^dag K != I (tolerance 1e-10) */
+  QT_ERR_OUT_OF_MEMORY = -3, /* allocator or budget refused */
+  QT_ERR_CUDA = -4,          /* CUDA runtime error (message names the call) */
+  QT_ERR_TIMEOUT = -5,       /* a bounded device wait ran out */
+  QT_ERR_UNSUPPORTED = -6,   /* valid request outside this build's limits */
+  QT_ERR_INTERNAL = -7       /* device-side consistency check failed */
+} qt_status;
+
+typedef enum { QT_OP_GATE = 0, QT_OP_KRAUS = 1, QT_OP_MIXTURE = 2 } qt_op_kind;
+typedef enum { QT_DELAYED = 0, QT_EAGER = 1 } qt_mode;
+typedef enum { QT_FP32 = 0, QT_TF32X3 = 1 } qt_precision;
+#define QT_FLAG_TIME_KERNELS 1u
+
+#define QT_MAX_QUBITS 34      /* largest state: 2^34 complex64 = 128 GiB */
+#define QT_MAX_OP_QUBITS 6    /* widest gate or channel */
+#define QT_MAX_FUSED_QUBITS 6 /* widest fused gate */
+
+/* One operation of a moment (Sec. II): a gate, a Kraus channel
+ * (KrausChannel) or a mixed-unitary channel (MixedUnitaryChannel). */
+typedef struct {
+  int32_t kind;            /* qt_op_kind */
+  uint32_t moment;         /* ops of one moment act on disjoint qubits */
+  uint32_t num_qubits;     /* 1..QT_MAX_OP_QUBITS */
+  uint32_t qubits[QT_MAX_OP_QUBITS];
+  uint32_t num_ops;        /* 1 for a gate; Kraus operators / mixture terms */
+  const double* probs;     /* MIXTURE: num_ops probabilities summing to 1 (+-1e-12) */
+  const double* mats;      /* num_ops matrices, 2^q x 2^q, row-major, (re,im) FP64 */
+} qt_op;
+
+typedef struct qt_circuit qt_circuit;
+typedef struct qt_fused qt_fused;
+typedef struct qt_run qt_run;
+typedef struct qt_server qt_server;
+
+/* Build and validate a noisy circuit (Sec. II; channel terms Sec. III.E).
+ * Checks qubit ranges, disjointness within each moment, sum K^dag K = I for
+ * Kraus channels (1e-10) and sum p = 1 for mixtures (1e-12, then
+ * renormalized).  Computes the lower bounds pbar_i = sigma_min(K_i)^2 of
+ * Sec. III.E (mixtures: pbar_i = p_i, so s = 1).  All input arrays are
+ * copied.  Errors: QT_ERR_INVALID_ARG, QT_ERR_NOT_CPTP. */
+qt_status qt_circuit_create(uint32_t num_qubits, uint32_t num_ops, const qt_op* ops,
+                            qt_circuit** out);
+
+/* Gate fusion (Sec. III.B): greedily merge operations that are close in
+ * space and time into fused gates of at most max_fused_qubits qubits
+ * (1..6; 0 = automatic choice).  Channels become slots of the fused gates;
+ * the matrix of each fused gate with every slot on its most likely
+ * (largest pbar) operator is precomputed.  The circuit must outlive the
+ * fused handle.  Errors: QT_ERR_INVALID_ARG. */
+qt_status qt_fuse(const qt_circuit* c, uint32_t max_fused_qubits, qt_fused** out);
+
+/* Parameters of a trajectory run. */
+typedef struct {
+  uint64_t seed;               /* Philox key */
+  uint64_t first_traj;         /* trajectory ids first_traj .. first_traj+num_traj-1 */
+  uint32_t num_traj;
+  uint32_t mode;               /* QT_DELAYED (Alg. 2) or QT_EAGER (conventional) */
+  uint32_t precision;          /* QT_FP32, or QT_TF32X3 for 5-6 qubit fused gates */
+  uint32_t samples_per_traj;   /* bitstrings drawn from each final state */
+  uint32_t num_z_masks;        /* Z-string expectations on each final state */
+  const uint64_t* z_masks;     /* num_z_masks masks (copied) */
+  uint32_t keep_states;        /* 1: keep every final state on the device */
+  uint32_t flags;              /* QT_FLAG_TIME_KERNELS: time each fused-gate launch */
+  void* stream;                /* cudaStream_t (0 = legacy default stream) */
+  uint64_t timeout_ns;         /* bound on any device wait (0 = 10 s) */
+} qt_run_params;
+
+/* Run num_traj trajectories of Alg. 2 (QT_DELAYED) or of the conventional
+ * algorithm (QT_EAGER, every channel evaluated immediately; branch choice
+ * from the same two-stage partition of [0,1)).  Per channel c the draw is
+ * r = u01(seed, traj, stream 0, index c); stage 1 picks the first i with
+ * r < pbar_i after subtracting the earlier pbar's and defers K_i; otherwise
+ * the deferred operators are applied, N = <psi|psi> and
+ * P_i = <psi|K_i^dag K_i|psi> are evaluated in one in-place pass, and
+ * K_i / sqrt(P_i) is applied for the first i with r < P_i/N - pbar_i.
+ * Requested samples and expectations are evaluated on each final state.
+ * Blocks until the results are on the host.  Errors: QT_ERR_INVALID_ARG,
+ * QT_ERR_OUT_OF_MEMORY, QT_ERR_CUDA, QT_ERR_UNSUPPORTED. */
+qt_status qt_run_trajectories(const qt_fused* f, const qt_run_params* p, qt_run** out);
+
+/* Bitstrings of the run: out[t * S + j] is sample j of trajectory t, bit k
+ * = qubit k; the smallest x with u_j * C(2^n - 1) < C(x), C the cumulative
+ * sum of |psi_x|^2 in index order (FP64), u_j = u01(seed, traj, 1, j).
+ * S must equal the run's samples_per_traj, or, if the run kept its states,
+ * any S (drawn now).  out holds num_traj * S entries. */
+qt_status qt_sample(qt_run* r, uint32_t samples_per_traj, uint64_t* out);
+
+/* Z-string expectations <psi| Z^{mask} |psi> / <psi|psi> of each final
+ * state: out[t * num_terms + m].  The masks must equal the run's z_masks,
+ * or, if the run kept its states, be any masks (evaluated now). */
+qt_status qt_expectation(qt_run* r, uint32_t num_terms, const uint64_t* z_masks,
+                         double* out);
+
+/* Per-trajectory records of a run (Sec. II "measurement key": the index of
+ * the selected Kraus operator).  kraus: num_traj * num_channels int32
+ * (channel order = circuit order); stage: same shape, 1 = decided by the
+ * lower bounds, 2 = decided by evaluated probabilities; cap = entries
+ * available in each array (either may be NULL). */
+qt_status qt_run_kraus_indices(const qt_run* r, int32_t* kraus, int32_t* stage, size_t cap);
+
+/* Statistics of a run. */
+typedef struct {
+  uint32_t num_traj, num_channels;
+  uint64_t fused_passes;      /* fused-gate kernel launches (state passes) */
+  uint64_t prob_passes;       /* probability-evaluation passes (Alg. 2 step 14) */
+  uint64_t gate_ops;          /* unfused gates applied (gate-equivalents) */
+  uint64_t flushes;           /* channels decided in stage 2 */
+  double device_ms;           /* device time of the trajectory loop (events) */
+  double apply_ms;            /* device time inside fused-gate kernels
+                                 (QT_FLAG_TIME_KERNELS, else 0) */
+  uint64_t apply_bytes;       /* algorithmic bytes of those kernels: 16 per
+                                 amplitude per pass (read + write, complex64) */
+  uint64_t h2d_bytes;         /* host->device bytes (copies + matrix parameters) */
+  uint64_t d2h_bytes;         /* device->host bytes */
+  uint64_t kernel_launches;   /* kernels of this library launched by the run */
+} qt_run_stats_t;
+qt_status qt_run_stats(const qt_run* r, qt_run_stats_t* out);
+
+/* Normalized final state of trajectory `traj` (index within the run) as
+ * complex64 (re, im float pairs); needs keep_states; dst is host memory of
+ * bytes >= 8 * 2^n. */
+qt_status qt_run_state(const qt_run* r, uint32_t traj, void* dst, size_t bytes);
+
+/* Device allocator (e.g. a framework's caching allocator).  alloc returns
+ * device memory of at least `bytes` usable on `stream`, or NULL; free
+ * releases it.  Passing NULLs restores the default (cudaMallocAsync). */
+typedef void* (*qt_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*qt_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+qt_status qt_set_allocator(qt_alloc_fn alloc, qt_free_fn free_fn, void* ctx);
+
+void qt_circuit_destroy(qt_circuit* c);
+void qt_fused_destroy(qt_fused* f);
+void qt_run_destroy(qt_run* r);
+const char* qt_last_error(void);
+
+/* Introspection of the fused plan (host only, no GPU needed). */
+typedef struct {
+  uint32_t num_fused, max_width, num_ops, num_channels;
+} qt_fused_info_t;
+qt_status qt_fused_info(const qt_fused* f, qt_fused_info_t* out);
+/* Fused gate g: its target qubits (sorted, <= 6), the op indices it contains
+ * (circuit order positions, members[] of length cap) and its default matrix
+ * (2^w x 2^w row-major (re,im) FP64, NULL to skip). */
+qt_status qt_fused_gate(const qt_fused* f, uint32_t g, uint32_t* width, uint32_t* targets,
+                        uint32_t* num_members, uint32_t* members, size_t cap, double* matrix);
+/* Lower bounds pbar_i of channel c (circuit order), cap entries. */
+qt_status qt_channel_lower_bounds(const qt_circuit* c, uint32_t channel, double* pbar,
+                                  size_t cap, uint32_t* num_ops);
+
+/* ---------------------------------------------------------------------- */
+/* State-level calls: the hot kernels on a caller-owned device state      */
+/* (complex64, 2^n amplitudes, 16-byte aligned).                           */
+/* ---------------------------------------------------------------------- */
+
+/* Alg. 1: state <- U on qubits[0..q-1] (q <= 6); U host FP64 (re,im). */
+qt_status qt_state_apply(void* state, uint32_t n, uint32_t q, const uint32_t* qubits,
+                         const double* U, uint32_t precision, void* stream);
+/* Reduced density block of qubits Q (q <= 3): rho[b][a] = sum_rest
+ * psi[rest,b] conj(psi[rest,a]), FP64 accumulation; out host (re,im) FP64
+ * 4^q complex, row-major.  P_i = tr(K_i^dag K_i rho) (Alg. 2 step 14). */
+qt_status qt_state_reduced_density(const void* state, uint32_t n, uint32_t q,
+                                   const uint32_t* qubits, double* out, void* stream);
+/* S bitstrings from |psi|^2 with uniforms u01(seed, traj, 1, j); out host. */
+qt_status qt_state_sample(const void* state, uint32_t n, uint64_t seed, uint64_t traj,
+                          uint32_t S, uint64_t* out, void* stream);
+/* Z-string expectations of the state (normalized by <psi|psi>); out host. */
+qt_status qt_state_expect_z(const void* state, uint32_t n, uint32_t num_terms,
+                            const uint64_t* z_masks, double* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QT_H */

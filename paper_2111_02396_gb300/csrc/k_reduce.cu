@@ -1,0 +1,463 @@
+// Read-only passes over the state: branch probabilities (Alg. 2 step 14),
+// Z-string expectations and bitstring sampling, plus state init / scale.
+//
+// Precision: products are formed in FP32 from the complex64 state; partial
+// sums over a short run of terms stay in FP32 and are then carried in FP64
+// (FP64 throughput on this part is low, so it is used only at that coarse
+// grain).  Every reduction has a fixed grid and a fixed combination order,
+// so results are bitwise reproducible run to run.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "kernels.h"
+#include "qt_philox.h"
+
+namespace qt {
+
+size_t scratch_partial_bytes() { return sizeof(double) * kMaxRedBlocks * 64; }
+
+// ---------------------------------------------------------------------------
+// block-wide FP64 reduction of W per-thread values into partial[block][W]
+// ---------------------------------------------------------------------------
+template <int W>
+__device__ __forceinline__ void block_reduce_store(double (&acc)[W], double* __restrict__ partial) {
+  __shared__ double sm[kRedThreads / 32][W];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < W; ++c) {
+    double v = acc[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sm[warp][c] = v;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < W; c += blockDim.x) {
+    double v = 0.0;
+    for (int w = 0; w < kRedThreads / 32; ++w) v += sm[w][c];
+    partial[static_cast<size_t>(blockIdx.x) * W + c] = v;
+  }
+}
+
+__global__ void k_finalize(const double* __restrict__ partial, int nblocks, int W,
+                           double* __restrict__ out) {
+  for (int c = threadIdx.x; c < W; c += blockDim.x) {
+    double v = 0.0;
+    for (int b = 0; b < nblocks; ++b) v += partial[static_cast<size_t>(b) * W + c];
+    out[c] = v;
+  }
+}
+
+template <typename Kern>
+static int red_grid(Kern kern, uint64_t work_items) {
+  // one full wave of resident blocks, capped by the work and by the scratch
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kRedThreads, 0);
+  if (occ <= 0) occ = 1;
+  uint64_t g = static_cast<uint64_t>(sm_count()) * occ;
+  const uint64_t need = (work_items + kRedThreads - 1) / kRedThreads;
+  if (g > need) g = need;
+  if (g > static_cast<uint64_t>(kMaxRedBlocks)) g = kMaxRedBlocks;
+  if (g < 1) g = 1;
+  return static_cast<int>(g);
+}
+
+// ---------------------------------------------------------------------------
+// Reduced density block of qubits Q: rho[b][a] = sum_rest psi[rest,b] conj(psi[rest,a]).
+// W = 4^q reals: the 2^q diagonal entries, then (re, im) of each b < a.
+// ---------------------------------------------------------------------------
+template <int Q>
+struct RdmArgs {
+  uint64_t offs[1 << Q];
+  uint32_t ins[Q];
+  uint64_t num_sets;
+};
+
+constexpr int kRdmChunk = 16;   // sets summed in FP32 before the FP64 carry
+
+template <int Q>
+__global__ void __launch_bounds__(kRedThreads) k_rdm(const float2* __restrict__ psi,
+                                                     const __grid_constant__ RdmArgs<Q> a,
+                                                     double* __restrict__ partial) {
+  constexpr int D = 1 << Q, W = D * D;
+  double acc[W];
+  float f[W];
+#pragma unroll
+  for (int c = 0; c < W; ++c) { acc[c] = 0.0; f[c] = 0.f; }
+  int cnt = 0;
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < a.num_sets;
+       i += stride) {
+    uint64_t base = i;
+#pragma unroll
+    for (int b = 0; b < Q; ++b) {
+      const uint32_t s = a.ins[b];
+      base = ((base >> s) << (s + 1)) | (base & ((1ull << s) - 1ull));
+    }
+    float2 v[D];
+#pragma unroll
+    for (int m = 0; m < D; ++m) v[m] = __ldg(psi + base + a.offs[m]);
+    int c = 0;
+#pragma unroll
+    for (int b = 0; b < D; ++b) { f[c] = fmaf(v[b].x, v[b].x, fmaf(v[b].y, v[b].y, f[c])); ++c; }
+#pragma unroll
+    for (int b = 0; b < D; ++b)
+#pragma unroll
+      for (int aa = b + 1; aa < D; ++aa) {
+        // v_b conj(v_a)
+        f[c] = fmaf(v[b].x, v[aa].x, fmaf(v[b].y, v[aa].y, f[c])); ++c;
+        f[c] = fmaf(v[b].y, v[aa].x, fmaf(-v[b].x, v[aa].y, f[c])); ++c;
+      }
+    if (++cnt == kRdmChunk) {
+#pragma unroll
+      for (int k = 0; k < W; ++k) { acc[k] += static_cast<double>(f[k]); f[k] = 0.f; }
+      cnt = 0;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < W; ++k) acc[k] += static_cast<double>(f[k]);
+  block_reduce_store<W>(acc, partial);
+}
+
+template <int Q>
+static cudaError_t rdm_q(const float2* psi, int n, const uint32_t* qubits, const Scratch& scr,
+                         cudaStream_t st) {
+  RdmArgs<Q> a;
+  uint32_t s[Q];
+  for (int b = 0; b < Q; ++b) s[b] = qubits[b];
+  for (int i = 1; i < Q; ++i)
+    for (int j = i; j > 0 && s[j - 1] > s[j]; --j) { const uint32_t t = s[j]; s[j] = s[j - 1]; s[j - 1] = t; }
+  for (int b = 0; b < Q; ++b) a.ins[b] = s[b];
+  for (int m = 0; m < (1 << Q); ++m) {
+    uint64_t o = 0;
+    for (int b = 0; b < Q; ++b)
+      if ((m >> b) & 1) o |= 1ull << qubits[b];
+    a.offs[m] = o;
+  }
+  a.num_sets = 1ull << (n - Q);
+  static int grid = 0;
+  static std::once_flag once;
+  std::call_once(once, [] { grid = red_grid(k_rdm<Q>, ~0ull >> 1); });
+  const uint64_t need = (a.num_sets + kRedThreads - 1) / kRedThreads;
+  const int g = static_cast<int>(need < static_cast<uint64_t>(grid) ? need : grid);
+  k_rdm<Q><<<g, kRedThreads, 0, st>>>(psi, a, scr.partial);
+  k_finalize<<<1, 64, 0, st>>>(scr.partial, g, 1 << (2 * Q), scr.result);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rdm(const float2* psi, int n, int q, const uint32_t* qubits, const Scratch& scr,
+                       cudaStream_t st) {
+  if (q > n) return cudaErrorInvalidValue;
+  switch (q) {
+    case 1: return rdm_q<1>(psi, n, qubits, scr, st);
+    case 2: return rdm_q<2>(psi, n, qubits, scr, st);
+    case 3: return rdm_q<3>(psi, n, qubits, scr, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+void rdm_unpack(int q, const double* r, double* rho) {
+  const int D = 1 << q;
+  int c = 0;
+  for (int b = 0; b < D; ++b) {
+    rho[2 * (b * D + b)] = r[c++];
+    rho[2 * (b * D + b) + 1] = 0.0;
+  }
+  for (int b = 0; b < D; ++b)
+    for (int a = b + 1; a < D; ++a) {
+      const double re = r[c++], im = r[c++];
+      rho[2 * (b * D + a)] = re;        // rho[b][a] = sum psi_b conj(psi_a)
+      rho[2 * (b * D + a) + 1] = im;
+      rho[2 * (a * D + b)] = re;        // Hermitian
+      rho[2 * (a * D + b) + 1] = -im;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Z-string expectations: result[0] = N, result[1+m] = sum_x |psi_x|^2 (-1)^popc(x & mask_m)
+// ---------------------------------------------------------------------------
+struct ExpArgs {
+  uint64_t masks[kExpGroup];
+  int nm;
+  uint64_t num_pairs;
+};
+
+constexpr int kExpChunk = 64;
+
+__global__ void __launch_bounds__(kRedThreads) k_expect(const float2* __restrict__ psi,
+                                                        const __grid_constant__ ExpArgs a,
+                                                        double* __restrict__ partial) {
+  constexpr int W = kExpGroup + 1;
+  double acc[W];
+  float f[W];
+#pragma unroll
+  for (int c = 0; c < W; ++c) { acc[c] = 0.0; f[c] = 0.f; }
+  int cnt = 0;
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < a.num_pairs;
+       i += stride) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(psi) + i);
+    const float w0 = fmaf(v.x, v.x, v.y * v.y), w1 = fmaf(v.z, v.z, v.w * v.w);
+    const uint64_t x0 = 2 * i;
+    f[0] += w0 + w1;
+#pragma unroll
+    for (int m = 0; m < kExpGroup; ++m) {
+      if (m < a.nm) {
+        const uint64_t mk = a.masks[m];
+        const int s0 = __popcll(x0 & mk) & 1;
+        const int s1 = s0 ^ static_cast<int>(mk & 1ull);
+        f[1 + m] += (s0 ? -w0 : w0) + (s1 ? -w1 : w1);
+      }
+    }
+    if (++cnt == kExpChunk) {
+#pragma unroll
+      for (int k = 0; k < W; ++k) { acc[k] += static_cast<double>(f[k]); f[k] = 0.f; }
+      cnt = 0;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < W; ++k) acc[k] += static_cast<double>(f[k]);
+  block_reduce_store<W>(acc, partial);
+}
+
+cudaError_t launch_expect(const float2* psi, int n, int nm, const uint64_t* masks,
+                          const Scratch& scr, cudaStream_t st) {
+  if (nm > kExpGroup || n < 1) return cudaErrorInvalidValue;
+  ExpArgs a;
+  for (int m = 0; m < kExpGroup; ++m) a.masks[m] = m < nm ? masks[m] : 0;
+  a.nm = nm;
+  a.num_pairs = 1ull << (n - 1);
+  static int grid = 0;
+  static std::once_flag once;
+  std::call_once(once, [] { grid = red_grid(k_expect, ~0ull >> 1); });
+  const uint64_t need = (a.num_pairs + kRedThreads - 1) / kRedThreads;
+  const int g = static_cast<int>(need < static_cast<uint64_t>(grid) ? need : grid);
+  k_expect<<<g, kRedThreads, 0, st>>>(psi, a, scr.partial);
+  k_finalize<<<1, 64, 0, st>>>(scr.partial, g, kExpGroup + 1, scr.result);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Sampling.  C(x) is built in three levels with one fixed arithmetic, used
+// both to build the block table and to search inside a block, so that the
+// search sees the same cumulative values the table was built from:
+//   chunk      64 amplitudes, warp inclusive scan in FP32 of (|a0|^2+|a1|^2)
+//   sub-block  16 chunks, running FP32 sum of chunk totals  -> cdf_sub
+//   block      64 sub-blocks, warp inclusive scan in FP64   -> block totals
+//   table      inclusive FP64 scan of the block totals      -> cdf_cum
+// A sample with uniform u targets t = u * C(2^n - 1) and returns the
+// smallest x with t < C(x).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float warp_incl_scan_f(float v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += y;
+  }
+  return v;
+}
+
+__device__ __forceinline__ double warp_incl_scan_d(double v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += y;
+  }
+  return v;
+}
+
+// weights of the two amplitudes a lane owns in a chunk (0 past the end)
+__device__ __forceinline__ void chunk_weights(const float2* __restrict__ psi, uint64_t namps,
+                                              uint64_t x0, float& w0, float& w1) {
+  w0 = 0.f;
+  w1 = 0.f;
+  if (x0 < namps) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(psi + x0));
+    w0 = fmaf(v.x, v.x, v.y * v.y);
+    w1 = fmaf(v.z, v.z, v.w * v.w);
+  }
+}
+
+__global__ void k_cdf_sub(const float2* __restrict__ psi, uint64_t namps, uint64_t nsub,
+                          float* __restrict__ sub) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (uint64_t s = warp; s < nsub; s += nwarps) {
+    float run = 0.f;
+    for (int c = 0; c < (1 << (kCdfSubLog - kCdfChunkLog)); ++c) {
+      const uint64_t x0 = (s << kCdfSubLog) + (static_cast<uint64_t>(c) << kCdfChunkLog) + 2 * lane;
+      float w0, w1;
+      chunk_weights(psi, namps, x0, w0, w1);
+      const float incl = warp_incl_scan_f(w0 + w1, lane);
+      run += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0) sub[s] = run;
+  }
+}
+
+// lane values of block b: (double)sub[2L] + (double)sub[2L+1]
+__device__ __forceinline__ void block_lane_values(const float* __restrict__ sub, uint64_t nsub,
+                                                  uint64_t b, int lane, double& s0, double& s1) {
+  const uint64_t i0 = (b << 6) + 2 * lane;
+  s0 = i0 < nsub ? static_cast<double>(sub[i0]) : 0.0;
+  s1 = i0 + 1 < nsub ? static_cast<double>(sub[i0 + 1]) : 0.0;
+}
+
+__global__ void k_cdf_blk(const float* __restrict__ sub, uint64_t nsub, uint64_t nblk,
+                          double* __restrict__ cum) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (uint64_t b = warp; b < nblk; b += nwarps) {
+    double s0, s1;
+    block_lane_values(sub, nsub, b, lane, s0, s1);
+    const double incl = warp_incl_scan_d(s0 + s1, lane);
+    if (lane == 31) cum[b] = incl;
+  }
+}
+
+// in-place inclusive scan of nblk doubles by one block of 1024 threads
+__global__ void __launch_bounds__(1024) k_cdf_scan(double* __restrict__ cum, uint64_t nblk) {
+  __shared__ double tot[1024];
+  const uint64_t per = (nblk + 1023) / 1024;
+  const uint64_t lo = threadIdx.x * per;
+  const uint64_t hi = lo + per < nblk ? lo + per : nblk;
+  double s = 0.0;
+  for (uint64_t i = lo; i < hi; ++i) s += cum[i];
+  tot[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int t = 0; t < 1024; ++t) { const double v = tot[t]; tot[t] = r; r += v; }
+  }
+  __syncthreads();
+  double r = tot[threadIdx.x];
+  for (uint64_t i = lo; i < hi; ++i) { r += cum[i]; cum[i] = r; }
+}
+
+__global__ void k_sample(const float2* __restrict__ psi, uint64_t namps, const float* __restrict__ sub,
+                         uint64_t nsub, const double* __restrict__ cum, uint64_t nblk, uint64_t seed,
+                         uint64_t traj, uint32_t S, uint64_t* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (uint64_t j = warp; j < S; j += nwarps) {
+    const double total = cum[nblk - 1];
+    const double t = uniform01(seed, traj, kStreamSample, static_cast<uint32_t>(j)) * total;
+    // block: first b with t < cum[b]
+    uint64_t lo = 0, hi = nblk - 1;
+    while (lo < hi) {
+      const uint64_t mid = (lo + hi) >> 1;
+      if (t < cum[mid]) hi = mid; else lo = mid + 1;
+    }
+    const uint64_t b = lo;
+    double trel = t - (b ? cum[b - 1] : 0.0);
+    // sub-block inside the block (same lane values and scan as k_cdf_blk)
+    double s0, s1;
+    block_lane_values(sub, nsub, b, lane, s0, s1);
+    const double incl = warp_incl_scan_d(s0 + s1, lane);
+    double excl = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (lane == 0) excl = 0.0;
+    unsigned hit = __ballot_sync(0xffffffffu, trel < incl);
+    int L = hit ? __ffs(hit) - 1 : 31;
+    const double eL = __shfl_sync(0xffffffffu, excl, L);
+    const double s0L = __shfl_sync(0xffffffffu, s0, L);
+    uint64_t sidx = (b << 6) + 2 * L;
+    double base = eL;
+    if (!(trel < eL + s0L)) { base = eL + s0L; sidx += 1; }
+    if (sidx >= nsub) sidx = nsub - 1;
+    trel -= base;
+    // chunks inside the sub-block (same chunk arithmetic as k_cdf_sub)
+    float run = 0.f;
+    uint64_t x = ~0ull, last_nz = sidx << kCdfSubLog;
+    for (int c = 0; c < (1 << (kCdfSubLog - kCdfChunkLog)); ++c) {
+      const uint64_t x0 = (sidx << kCdfSubLog) + (static_cast<uint64_t>(c) << kCdfChunkLog) + 2 * lane;
+      float w0, w1;
+      chunk_weights(psi, namps, x0, w0, w1);
+      const float inc = warp_incl_scan_f(w0 + w1, lane);
+      const float tot = __shfl_sync(0xffffffffu, inc, 31);
+      const float cend = run + inc;
+      const float cstart = cend - (w0 + w1);
+      const unsigned h = __ballot_sync(0xffffffffu, trel < static_cast<double>(cend));
+      const unsigned nz = __ballot_sync(0xffffffffu, (w0 + w1) > 0.f);
+      if (nz) {
+        const int ln = 31 - __clz(nz);
+        const float w1n = __shfl_sync(0xffffffffu, w1, ln);
+        last_nz = (sidx << kCdfSubLog) + (static_cast<uint64_t>(c) << kCdfChunkLog) + 2 * ln + (w1n > 0.f ? 1 : 0);
+      }
+      if (h) {
+        const int l2 = __ffs(h) - 1;
+        const float cs = __shfl_sync(0xffffffffu, cstart, l2);
+        const float a0 = __shfl_sync(0xffffffffu, w0, l2);
+        x = (sidx << kCdfSubLog) + (static_cast<uint64_t>(c) << kCdfChunkLog) + 2 * l2 +
+            (trel < static_cast<double>(cs + a0) ? 0 : 1);
+        break;
+      }
+      run += tot;
+    }
+    if (x == ~0ull) x = last_nz;     // rounding put t past the sub-block end
+    if (lane == 0) out[j] = x;
+  }
+}
+
+cudaError_t launch_sample(const float2* psi, int n, uint64_t seed, uint64_t traj, uint32_t S,
+                          uint64_t* out, const Scratch& scr, cudaStream_t st) {
+  if (n < 1) return cudaErrorInvalidValue;
+  const uint64_t namps = 1ull << n;
+  const uint64_t nsub = cdf_num_sub(n), nblk = cdf_num_blk(n);
+  const int threads = 256, wpb = threads / 32;
+  uint64_t g = (nsub + wpb - 1) / wpb;
+  const uint64_t cap = static_cast<uint64_t>(sm_count()) * 8;
+  if (g > cap) g = cap;
+  k_cdf_sub<<<static_cast<unsigned>(g), threads, 0, st>>>(psi, namps, nsub, scr.cdf_sub);
+  uint64_t gb = (nblk + wpb - 1) / wpb;
+  if (gb > cap) gb = cap;
+  k_cdf_blk<<<static_cast<unsigned>(gb), threads, 0, st>>>(scr.cdf_sub, nsub, nblk, scr.cdf_cum);
+  k_cdf_scan<<<1, 1024, 0, st>>>(scr.cdf_cum, nblk);
+  if (S > 0) {
+    uint64_t gs = (S + wpb - 1) / wpb;
+    if (gs > cap) gs = cap;
+    k_sample<<<static_cast<unsigned>(gs), threads, 0, st>>>(psi, namps, scr.cdf_sub, nsub, scr.cdf_cum,
+                                                           nblk, seed, traj, S, out);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_init(float4* __restrict__ psi, uint64_t npairs) {
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < npairs; i += stride)
+    psi[i] = make_float4(i == 0 ? 1.f : 0.f, 0.f, 0.f, 0.f);
+}
+
+__global__ void k_scale(float4* __restrict__ psi, uint64_t npairs, float f) {
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < npairs; i += stride) {
+    float4 v = psi[i];
+    v.x *= f; v.y *= f; v.z *= f; v.w *= f;
+    psi[i] = v;
+  }
+}
+
+static unsigned stream_grid(uint64_t items) {
+  uint64_t g = (items + 255) / 256;
+  const uint64_t cap = static_cast<uint64_t>(sm_count()) * 8;
+  return static_cast<unsigned>(g < cap ? (g ? g : 1) : cap);
+}
+
+cudaError_t launch_init_state(float2* psi, int n, cudaStream_t st) {
+  if (n < 1) return cudaErrorInvalidValue;
+  const uint64_t np = 1ull << (n - 1);
+  k_init<<<stream_grid(np), 256, 0, st>>>(reinterpret_cast<float4*>(psi), np);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale(float2* psi, int n, float f, cudaStream_t st) {
+  if (n < 1) return cudaErrorInvalidValue;
+  const uint64_t np = 1ull << (n - 1);
+  k_scale<<<stream_grid(np), 256, 0, st>>>(reinterpret_cast<float4*>(psi), np, f);
+  return cudaGetLastError();
+}
+
+}  // namespace qt

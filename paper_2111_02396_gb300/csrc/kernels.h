@@ -1,0 +1,54 @@
+// Launchers of the sm_103a kernels (host-callable, C++ linkage).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qt.h"
+
+namespace qt {
+
+// ---- device scratch sizes -------------------------------------------------
+constexpr int kRedThreads = 256;          // threads of the reduction kernels
+constexpr int kMaxRedBlocks = 152 * 8;    // upper bound of their grid
+constexpr int kRdmMaxQ = 3;               // reduced density matrix: q <= 3
+constexpr int kExpGroup = 16;             // Z masks per expectation pass
+// CDF for sampling: chunk = 64 amplitudes (one warp, 128-bit loads),
+// sub-block = 16 chunks, block = 64 sub-blocks
+constexpr int kCdfChunkLog = 6, kCdfSubLog = 10, kCdfBlkLog = 16;
+
+inline uint64_t cdf_num_sub(int n) { return ((1ull << n) + (1ull << kCdfSubLog) - 1) >> kCdfSubLog; }
+inline uint64_t cdf_num_blk(int n) { return (cdf_num_sub(n) + 63) >> 6; }
+
+struct Scratch {
+  double* partial = nullptr;   // kMaxRedBlocks * 64 doubles
+  double* result = nullptr;    // 64 doubles
+  float* cdf_sub = nullptr;    // cdf_num_sub(n) floats
+  double* cdf_cum = nullptr;   // cdf_num_blk(n) doubles
+};
+size_t scratch_partial_bytes();
+
+// ---- kernels ---------------------------------------------------------------
+// state <- U (2^k x 2^k row-major complex64, basis `targets` sorted ascending)
+cudaError_t launch_apply(float2* psi, int n, int k, const uint32_t* targets, const float2* U,
+                         cudaStream_t st);
+// rho (4^q doubles, layout of rdm_unpack) of qubits Q into scr.result
+cudaError_t launch_rdm(const float2* psi, int n, int q, const uint32_t* qubits, const Scratch& scr,
+                       cudaStream_t st);
+// N = <psi|psi> and sum |psi_x|^2 (-1)^popc(x&mask) for nm <= 16 masks into scr.result[0..nm]
+cudaError_t launch_expect(const float2* psi, int n, int nm, const uint64_t* masks,
+                          const Scratch& scr, cudaStream_t st);
+// S samples of trajectory traj into out (device)
+cudaError_t launch_sample(const float2* psi, int n, uint64_t seed, uint64_t traj, uint32_t S,
+                          uint64_t* out, const Scratch& scr, cudaStream_t st);
+// |0...0>
+cudaError_t launch_init_state(float2* psi, int n, cudaStream_t st);
+// psi *= f
+cudaError_t launch_scale(float2* psi, int n, float f, cudaStream_t st);
+
+// unpack the 4^q reals of an rdm result into a row-major complex matrix
+// rho[b][a] = sum psi_b conj(psi_a)
+void rdm_unpack(int q, const double* r, double* rho_interleaved);
+
+int sm_count();
+
+}  // namespace qt

@@ -1,0 +1,683 @@
+// Trajectory controller and C ABI (Sec. III.E, Alg. 2).
+//
+// Delayed inner products, as run here: stage 1 of every channel depends
+// only on its draw r and the lower bounds pbar, so all stage-1 decisions of
+// a trajectory are taken on the host before any kernel runs.  Channels that
+// stage 1 cannot decide ("flush points") cut the circuit into segments.
+// Each segment is applied as the fused gates restricted to the segment's
+// operations (a fused gate whose slots all hold their default operator and
+// that lies wholly inside the segment uses its precomputed matrix; any
+// other piece is recomposed on the host in FP64).  At a flush point one
+// read pass evaluates the reduced density block rho_Q of the channel's
+// qubits in FP64, which gives N = tr rho_Q and P_i = tr(K_i^dag K_i rho_Q)
+// for every branch at once; stage 2 then picks the branch and the operator
+// K_i / sqrt(P_i) becomes the first member of the next segment.  The
+// conventional (eager) algorithm is the same loop with every channel a
+// flush point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "kernels.h"
+#include "qt_internal.h"
+#include "qt_philox.h"
+
+namespace qt {
+
+// ---------------------------------------------------------------------------
+// device memory
+// ---------------------------------------------------------------------------
+struct Allocator {
+  qt_alloc_fn alloc = nullptr;
+  qt_free_fn free = nullptr;
+  void* ctx = nullptr;
+};
+static Allocator g_alloc;
+static std::mutex g_alloc_mu;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  Allocator a;
+  cudaStream_t st = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept { *this = std::move(o); }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) {
+      release();
+      p = o.p; bytes = o.bytes; a = o.a; st = o.st;
+      o.p = nullptr; o.bytes = 0;
+    }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  bool alloc(size_t b, cudaStream_t s) {
+    release();
+    {
+      std::lock_guard<std::mutex> lk(g_alloc_mu);
+      a = g_alloc;
+    }
+    st = s;
+    bytes = b;
+    if (a.alloc) {
+      p = a.alloc(b, s, a.ctx);
+    } else if (cudaMallocAsync(&p, b, s) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    return p != nullptr;
+  }
+  void release() {
+    if (!p) return;
+    if (a.alloc) {
+      if (a.free) a.free(p, bytes, st, a.ctx);
+    } else {
+      cudaFreeAsync(p, st);
+    }
+    p = nullptr;
+  }
+  template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+static qt_status cuda_fail(cudaError_t e, const char* where) {
+  return set_error(QT_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+#define QT_CUDA(call, where)                         \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+  } while (0)
+
+struct ScratchBufs {
+  DevBuf partial, result, sub, cum;
+  Scratch s;
+  bool alloc(int n, cudaStream_t st) {
+    if (!partial.alloc(scratch_partial_bytes(), st)) return false;
+    if (!result.alloc(sizeof(double) * 64, st)) return false;
+    if (!sub.alloc(sizeof(float) * cdf_num_sub(n), st)) return false;
+    if (!cum.alloc(sizeof(double) * cdf_num_blk(n), st)) return false;
+    s.partial = partial.as<double>();
+    s.result = result.as<double>();
+    s.cdf_sub = sub.as<float>();
+    s.cdf_cum = cum.as<double>();
+    return true;
+  }
+};
+
+static void to_f32(const std::vector<cd>& m, std::vector<float2>& out) {
+  out.resize(m.size());
+  for (size_t i = 0; i < m.size(); ++i)
+    out[i] = make_float2(static_cast<float>(m[i].real()), static_cast<float>(m[i].imag()));
+}
+
+}  // namespace qt
+
+using namespace qt;
+
+struct qt_run {
+  const qt_fused* f = nullptr;
+  qt_run_params p{};
+  std::vector<uint64_t> masks;
+  uint32_t n = 0, T = 0, nch = 0;
+  std::vector<int32_t> kraus, stage;
+  std::vector<uint64_t> samples;
+  std::vector<double> expect, norms;
+  std::vector<DevBuf> states;
+  ScratchBufs scr;
+  qt_run_stats_t stats{};
+  cudaStream_t st = nullptr;
+};
+
+namespace qt {
+
+// stage 1 / stage 2 of Alg. 2 on one draw.  P == nullptr: stage 1 only,
+// returns -1 when it does not decide.  Otherwise the two-stage partition of
+// [0,1): lower-bound intervals first, then intervals of width P_i/N - pbar_i.
+static int decide(const Op& op, double r, const double* P, double N, int* stage_out) {
+  double rr = r;
+  for (uint32_t i = 0; i < op.num_ops; ++i) {
+    if (rr < op.pbar[i]) { *stage_out = 1; return static_cast<int>(i); }
+    rr -= op.pbar[i];
+  }
+  if (!P) return -1;
+  *stage_out = 2;
+  int last = -1, last_pos = -1;
+  for (uint32_t i = 0; i < op.num_ops; ++i) {
+    double d = P[i] / N - op.pbar[i];
+    if (d < 0.0) d = 0.0;                    // rounding
+    if (d > 0.0) last = static_cast<int>(i);
+    if (P[i] > 0.0) last_pos = static_cast<int>(i);
+    if (rr < d) return static_cast<int>(i);
+    rr -= d;
+  }
+  return last >= 0 ? last : (last_pos >= 0 ? last_pos : op.def);
+}
+
+struct Controller {
+  qt_run& R;
+  const Circuit& c;
+  const Fused& f;
+  std::vector<std::vector<float2>> def32;   // default fused matrices in FP32
+  std::vector<cd> tmp;
+  std::vector<float2> tmp32;
+  double* pinned = nullptr;
+  std::vector<cudaEvent_t> ev;              // timing events (pairs)
+  size_t ev_used = 0;
+
+  explicit Controller(qt_run& r) : R(r), c(*r.f->c), f(*r.f) {
+    def32.resize(f.gates.size());
+    for (size_t g = 0; g < f.gates.size(); ++g) to_f32(f.gates[g].def, def32[g]);
+  }
+  ~Controller() {
+    if (pinned) cudaFreeHost(pinned);
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+
+  qt_status apply(float2* psi, const std::vector<uint32_t>& targets, const float2* U) {
+    const bool timed = (R.p.flags & QT_FLAG_TIME_KERNELS) != 0;
+    if (timed) {
+      if (ev_used + 2 > ev.size()) {
+        for (int k = 0; k < 2; ++k) {
+          cudaEvent_t e;
+          QT_CUDA(cudaEventCreate(&e), "cudaEventCreate");
+          ev.push_back(e);
+        }
+      }
+      QT_CUDA(cudaEventRecord(ev[ev_used], R.st), "cudaEventRecord");
+    }
+    QT_CUDA(launch_apply(psi, static_cast<int>(R.n), static_cast<int>(targets.size()), targets.data(), U, R.st),
+            "apply kernel launch");
+    if (timed) {
+      QT_CUDA(cudaEventRecord(ev[ev_used + 1], R.st), "cudaEventRecord");
+      ev_used += 2;
+    }
+    R.stats.fused_passes++;
+    R.stats.kernel_launches++;
+    R.stats.apply_bytes += 16ull << R.n;
+    const size_t d = 1ull << targets.size();
+    R.stats.h2d_bytes += sizeof(float2) * d * d;
+    return QT_OK;
+  }
+
+  qt_status collect_timing() {
+    if (!ev_used) return QT_OK;
+    QT_CUDA(cudaEventSynchronize(ev[ev_used - 1]), "cudaEventSynchronize");
+    double ms = 0.0;
+    for (size_t i = 0; i < ev_used; i += 2) {
+      float t = 0.f;
+      QT_CUDA(cudaEventElapsedTime(&t, ev[i], ev[i + 1]), "cudaEventElapsedTime");
+      ms += t;
+    }
+    R.stats.apply_ms += ms;
+    ev_used = 0;
+    return QT_OK;
+  }
+
+  // Apply ops [lo, hi) of the circuit.  choice[ch] is the operator of each
+  // channel; norm_scale[ch] > 0 marks a stage-2 choice applied as
+  // K_i * norm_scale (the Kraus form, normalized).
+  qt_status run_segment(float2* psi, uint32_t lo, uint32_t hi, const std::vector<int>& choice,
+                        const std::vector<double>& norm_scale) {
+    std::vector<std::pair<uint32_t, const cd*>> seq;
+    std::vector<std::vector<cd>> scaled;
+    for (size_t g = 0; g < f.gates.size(); ++g) {
+      const FusedGate& fg = f.gates[g];
+      seq.clear();
+      scaled.clear();
+      bool whole = true, dflt = true;
+      uint64_t mask = 0;
+      for (uint32_t m : fg.members) {
+        if (m < lo || m >= hi) { whole = false; continue; }
+        const Op& op = c.ops[m];
+        for (uint32_t b = 0; b < op.q; ++b) mask |= 1ull << op.qubits[b];
+        if (op.kind == QT_OP_GATE) {
+          seq.emplace_back(m, op.mat(0));
+          continue;
+        }
+        const int ch = op.channel;
+        const int ci = choice[ch];
+        if (norm_scale[ch] > 0.0) {
+          dflt = false;
+          const size_t dd = static_cast<size_t>(op.dim()) * op.dim();
+          scaled.emplace_back(op.kraus_op(static_cast<uint32_t>(ci)), op.kraus_op(static_cast<uint32_t>(ci)) + dd);
+          for (auto& x : scaled.back()) x *= norm_scale[ch];
+          seq.emplace_back(m, nullptr);      // patched below
+        } else {
+          if (ci != op.def) dflt = false;
+          seq.emplace_back(m, op.mat(static_cast<uint32_t>(ci)));
+        }
+      }
+      if (seq.empty()) continue;
+      size_t si = 0;
+      for (auto& e : seq)
+        if (!e.second) e.second = scaled[si++].data();
+      if (whole && dflt) {
+        qt_status s = apply(psi, fg.targets, def32[g].data());
+        if (s != QT_OK) return s;
+        continue;
+      }
+      std::vector<uint32_t> targets;
+      for (uint32_t q = 0; q < 64; ++q)
+        if (mask & (1ull << q)) targets.push_back(q);
+      compose(c, targets, seq, tmp);
+      to_f32(tmp, tmp32);
+      qt_status s = apply(psi, targets, tmp32.data());
+      if (s != QT_OK) return s;
+    }
+    return QT_OK;
+  }
+
+  // probability pass of channel op `oi`: returns N and P[0..num_ops)
+  qt_status probabilities(const float2* psi, uint32_t oi, double& N, double* P) {
+    const Op& op = c.ops[oi];
+    if (op.q > static_cast<uint32_t>(kRdmMaxQ))
+      return set_error(QT_ERR_UNSUPPORTED, "channel on %u qubits: probability pass supports <= 3", op.q);
+    QT_CUDA(launch_rdm(psi, static_cast<int>(R.n), static_cast<int>(op.q), op.qubits, R.scr.s, R.st),
+            "probability kernel launch");
+    const int W = 1 << (2 * op.q);
+    QT_CUDA(cudaMemcpyAsync(pinned, R.scr.s.result, sizeof(double) * W, cudaMemcpyDeviceToHost, R.st),
+            "cudaMemcpyAsync(probabilities)");
+    QT_CUDA(cudaStreamSynchronize(R.st), "cudaStreamSynchronize(probabilities)");
+    R.stats.prob_passes++;
+    R.stats.kernel_launches += 2;
+    R.stats.d2h_bytes += sizeof(double) * W;
+    const int D = static_cast<int>(op.dim());
+    double rho[2 * 64];
+    rdm_unpack(static_cast<int>(op.q), pinned, rho);
+    N = 0.0;
+    for (int b = 0; b < D; ++b) N += rho[2 * (b * D + b)];
+    for (uint32_t i = 0; i < op.num_ops; ++i) {
+      const cd* M = op.mtm_op(i);
+      double acc = 0.0;                     // tr(M rho) = sum_ab M[a][b] rho[b][a]
+      for (int a = 0; a < D; ++a)
+        for (int b = 0; b < D; ++b) {
+          const cd r(rho[2 * (b * D + a)], rho[2 * (b * D + a) + 1]);
+          acc += (M[a * D + b] * r).real();
+        }
+      P[i] = acc;
+    }
+    return QT_OK;
+  }
+
+  qt_status trajectory(uint32_t t, float2* psi) {
+    const uint64_t traj = R.p.first_traj + t;
+    const uint32_t nch = R.nch;
+    std::vector<int> choice(nch, 0);
+    std::vector<double> scale(nch, 0.0);
+    std::vector<double> rdraw(nch);
+    std::vector<uint32_t> flush_ops;
+    int32_t* kr = R.kraus.data() + static_cast<size_t>(t) * nch;
+    int32_t* sg = R.stage.data() + static_cast<size_t>(t) * nch;
+    for (uint32_t ch = 0; ch < nch; ++ch) {
+      const Op& op = c.ops[c.channel_op[ch]];
+      rdraw[ch] = uniform01(R.p.seed, traj, kStreamChannel, ch);
+      int st = 0;
+      const int ci = (R.p.mode == QT_DELAYED) ? decide(op, rdraw[ch], nullptr, 1.0, &st) : -1;
+      if (ci >= 0) {
+        choice[ch] = ci;
+        kr[ch] = ci;
+        sg[ch] = 1;
+      } else {
+        choice[ch] = op.def;
+        flush_ops.push_back(c.channel_op[ch]);
+      }
+    }
+    QT_CUDA(launch_init_state(psi, static_cast<int>(R.n), R.st), "init kernel launch");
+    R.stats.kernel_launches++;
+    uint32_t lo = 0;
+    const uint32_t nops = static_cast<uint32_t>(c.ops.size());
+    for (size_t k = 0; k <= flush_ops.size(); ++k) {
+      const uint32_t hi = k < flush_ops.size() ? flush_ops[k] : nops;
+      qt_status s = run_segment(psi, lo, hi, choice, scale);
+      if (s != QT_OK) return s;
+      if (k == flush_ops.size()) break;
+      const uint32_t oi = flush_ops[k];
+      const Op& op = c.ops[oi];
+      double N = 0.0, P[64];
+      s = probabilities(psi, oi, N, P);
+      if (s != QT_OK) return s;
+      int st = 2;
+      const int ci = decide(op, rdraw[op.channel], P, N, &st);
+      choice[op.channel] = ci;
+      scale[op.channel] = 1.0 / std::sqrt(P[ci] > 0.0 ? P[ci] : 1.0);
+      kr[op.channel] = ci;
+      sg[op.channel] = st;
+      R.stats.flushes += (st == 2);
+      lo = oi;
+    }
+    return QT_OK;
+  }
+
+  qt_status measure(uint32_t t, const float2* psi, uint64_t* d_samples) {
+    const uint64_t traj = R.p.first_traj + t;
+    const uint32_t M = static_cast<uint32_t>(R.masks.size());
+    double N = 0.0;
+    for (uint32_t g0 = 0; g0 < std::max<uint32_t>(M, 1); g0 += kExpGroup) {
+      const int nm = static_cast<int>(std::min<uint32_t>(kExpGroup, M - std::min(M, g0)));
+      QT_CUDA(launch_expect(psi, static_cast<int>(R.n), nm, R.masks.data() + std::min(M, g0), R.scr.s, R.st),
+              "expectation kernel launch");
+      QT_CUDA(cudaMemcpyAsync(pinned, R.scr.s.result, sizeof(double) * (kExpGroup + 1),
+                              cudaMemcpyDeviceToHost, R.st), "cudaMemcpyAsync(expectation)");
+      QT_CUDA(cudaStreamSynchronize(R.st), "cudaStreamSynchronize(expectation)");
+      R.stats.d2h_bytes += sizeof(double) * (kExpGroup + 1);
+      R.stats.kernel_launches += 2;
+      N = pinned[0];
+      for (int m = 0; m < nm; ++m) R.expect[static_cast<size_t>(t) * M + g0 + m] = pinned[1 + m] / N;
+    }
+    R.norms[t] = N;
+    if (R.p.samples_per_traj) {
+      QT_CUDA(launch_sample(psi, static_cast<int>(R.n), R.p.seed, traj, R.p.samples_per_traj,
+                            d_samples + static_cast<size_t>(t) * R.p.samples_per_traj, R.scr.s, R.st),
+              "sampling kernel launch");
+      R.stats.kernel_launches += 4;
+    }
+    return QT_OK;
+  }
+};
+
+}  // namespace qt
+
+extern "C" {
+
+qt_status qt_set_allocator(qt_alloc_fn alloc, qt_free_fn free_fn, void* ctx) {
+  clear_error();
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return set_error(QT_ERR_INVALID_ARG, "qt_set_allocator: give both functions or neither");
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc.alloc = alloc;
+  g_alloc.free = free_fn;
+  g_alloc.ctx = ctx;
+  return QT_OK;
+}
+
+qt_status qt_run_trajectories(const qt_fused* f, const qt_run_params* p, qt_run** out) {
+  clear_error();
+  if (!f || !p || !out) return set_error(QT_ERR_INVALID_ARG, "qt_run_trajectories: NULL argument");
+  *out = nullptr;
+  if (p->mode != QT_DELAYED && p->mode != QT_EAGER)
+    return set_error(QT_ERR_INVALID_ARG, "qt_run_trajectories: unknown mode %u", p->mode);
+  if (p->precision != QT_FP32 && p->precision != QT_TF32X3)
+    return set_error(QT_ERR_INVALID_ARG, "qt_run_trajectories: unknown precision %u", p->precision);
+  if (p->num_z_masks && !p->z_masks)
+    return set_error(QT_ERR_INVALID_ARG, "qt_run_trajectories: z_masks is NULL");
+  const Circuit& c = *f->c;
+  if (c.n < 1) return set_error(QT_ERR_INVALID_ARG, "qt_run_trajectories: empty circuit");
+  for (const auto& g : f->gates)
+    if (g.targets.size() > 5)
+      return set_error(QT_ERR_UNSUPPORTED, "qt_run_trajectories: fused width %zu > 5 not built", g.targets.size());
+  std::unique_ptr<qt_run> R(new (std::nothrow) qt_run());
+  if (!R) return set_error(QT_ERR_OUT_OF_MEMORY, "qt_run_trajectories: host allocation");
+  R->f = f;
+  R->p = *p;
+  R->p.z_masks = nullptr;
+  R->masks.assign(p->z_masks, p->z_masks + p->num_z_masks);
+  R->n = c.n;
+  R->T = p->num_traj;
+  R->nch = static_cast<uint32_t>(c.channel_op.size());
+  R->st = static_cast<cudaStream_t>(p->stream);
+  R->kraus.assign(static_cast<size_t>(R->T) * R->nch, -1);
+  R->stage.assign(static_cast<size_t>(R->T) * R->nch, 0);
+  R->samples.assign(static_cast<size_t>(R->T) * p->samples_per_traj, 0);
+  R->expect.assign(static_cast<size_t>(R->T) * R->masks.size(), 0.0);
+  R->norms.assign(R->T, 0.0);
+  R->stats.num_traj = R->T;
+  R->stats.num_channels = R->nch;
+  if (!R->scr.alloc(static_cast<int>(c.n), R->st))
+    return set_error(QT_ERR_OUT_OF_MEMORY, "qt_run_trajectories: scratch allocation");
+  const size_t sbytes = sizeof(float2) << c.n;
+  DevBuf work, dsamp;
+  if (!p->keep_states && !work.alloc(sbytes, R->st))
+    return set_error(QT_ERR_OUT_OF_MEMORY, "qt_run_trajectories: state allocation (%zu bytes)", sbytes);
+  if (p->keep_states) {
+    R->states.resize(R->T);
+    for (uint32_t t = 0; t < R->T; ++t)
+      if (!R->states[t].alloc(sbytes, R->st))
+        return set_error(QT_ERR_OUT_OF_MEMORY, "qt_run_trajectories: state %u allocation (%zu bytes)", t, sbytes);
+  }
+  const size_t nsamp = static_cast<size_t>(R->T) * p->samples_per_traj;
+  if (nsamp && !dsamp.alloc(sizeof(uint64_t) * nsamp, R->st))
+    return set_error(QT_ERR_OUT_OF_MEMORY, "qt_run_trajectories: sample buffer");
+  Controller ctl(*R);
+  QT_CUDA(cudaMallocHost(&ctl.pinned, sizeof(double) * 128), "cudaMallocHost");
+  cudaEvent_t e0, e1;
+  QT_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
+  QT_CUDA(cudaEventCreate(&e1), "cudaEventCreate");
+  struct EvGuard { cudaEvent_t a, b; ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); } } eg{e0, e1};
+  QT_CUDA(cudaEventRecord(e0, R->st), "cudaEventRecord");
+  for (uint32_t t = 0; t < R->T; ++t) {
+    float2* psi = p->keep_states ? R->states[t].as<float2>() : work.as<float2>();
+    qt_status s = ctl.trajectory(t, psi);
+    if (s != QT_OK) return s;
+    s = ctl.measure(t, psi, dsamp.as<uint64_t>());
+    if (s != QT_OK) return s;
+    s = ctl.collect_timing();
+    if (s != QT_OK) return s;
+  }
+  QT_CUDA(cudaEventRecord(e1, R->st), "cudaEventRecord");
+  if (nsamp) {
+    QT_CUDA(cudaMemcpyAsync(R->samples.data(), dsamp.p, sizeof(uint64_t) * nsamp, cudaMemcpyDeviceToHost, R->st),
+            "cudaMemcpyAsync(samples)");
+    R->stats.d2h_bytes += sizeof(uint64_t) * nsamp;
+  }
+  QT_CUDA(cudaStreamSynchronize(R->st), "cudaStreamSynchronize(run)");
+  float ms = 0.f;
+  QT_CUDA(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+  R->stats.device_ms = ms;
+  R->stats.gate_ops = f->gate_ops * R->T;
+  *out = R.release();
+  return QT_OK;
+}
+
+void qt_run_destroy(qt_run* r) { delete r; }
+
+qt_status qt_run_stats(const qt_run* r, qt_run_stats_t* out) {
+  clear_error();
+  if (!r || !out) return set_error(QT_ERR_INVALID_ARG, "qt_run_stats: NULL argument");
+  *out = r->stats;
+  return QT_OK;
+}
+
+qt_status qt_run_kraus_indices(const qt_run* r, int32_t* kraus, int32_t* stage, size_t cap) {
+  clear_error();
+  if (!r) return set_error(QT_ERR_INVALID_ARG, "qt_run_kraus_indices: NULL run");
+  const size_t need = r->kraus.size();
+  if ((kraus || stage) && cap < need)
+    return set_error(QT_ERR_INVALID_ARG, "qt_run_kraus_indices: cap %zu < %zu", cap, need);
+  if (kraus) std::memcpy(kraus, r->kraus.data(), sizeof(int32_t) * need);
+  if (stage) std::memcpy(stage, r->stage.data(), sizeof(int32_t) * need);
+  return QT_OK;
+}
+
+qt_status qt_sample(qt_run* r, uint32_t S, uint64_t* out) {
+  clear_error();
+  if (!r || (!out && S)) return set_error(QT_ERR_INVALID_ARG, "qt_sample: NULL argument");
+  if (S == r->p.samples_per_traj) {
+    std::memcpy(out, r->samples.data(), sizeof(uint64_t) * r->samples.size());
+    return QT_OK;
+  }
+  if (r->states.empty())
+    return set_error(QT_ERR_INVALID_ARG, "qt_sample: S=%u differs from the run's samples_per_traj=%u and states were not kept",
+                     S, r->p.samples_per_traj);
+  DevBuf d;
+  if (!d.alloc(sizeof(uint64_t) * S * r->T, r->st)) return set_error(QT_ERR_OUT_OF_MEMORY, "qt_sample: buffer");
+  for (uint32_t t = 0; t < r->T; ++t)
+    QT_CUDA(launch_sample(r->states[t].as<float2>(), static_cast<int>(r->n), r->p.seed, r->p.first_traj + t, S,
+                          d.as<uint64_t>() + static_cast<size_t>(t) * S, r->scr.s, r->st),
+            "sampling kernel launch");
+  QT_CUDA(cudaMemcpyAsync(out, d.p, sizeof(uint64_t) * S * r->T, cudaMemcpyDeviceToHost, r->st), "cudaMemcpyAsync");
+  QT_CUDA(cudaStreamSynchronize(r->st), "cudaStreamSynchronize");
+  return QT_OK;
+}
+
+qt_status qt_expectation(qt_run* r, uint32_t M, const uint64_t* masks, double* out) {
+  clear_error();
+  if (!r || (M && (!masks || !out))) return set_error(QT_ERR_INVALID_ARG, "qt_expectation: NULL argument");
+  if (M == r->masks.size() && std::equal(r->masks.begin(), r->masks.end(), masks)) {
+    std::memcpy(out, r->expect.data(), sizeof(double) * r->expect.size());
+    return QT_OK;
+  }
+  if (r->states.empty())
+    return set_error(QT_ERR_INVALID_ARG, "qt_expectation: masks differ from the run's and states were not kept");
+  double* pinned = nullptr;
+  QT_CUDA(cudaMallocHost(&pinned, sizeof(double) * (kExpGroup + 1)), "cudaMallocHost");
+  for (uint32_t t = 0; t < r->T; ++t)
+    for (uint32_t g0 = 0; g0 < M; g0 += kExpGroup) {
+      const int nm = static_cast<int>(std::min<uint32_t>(kExpGroup, M - g0));
+      cudaError_t e = launch_expect(r->states[t].as<float2>(), static_cast<int>(r->n), nm, masks + g0, r->scr.s, r->st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(pinned, r->scr.s.result, sizeof(double) * (kExpGroup + 1), cudaMemcpyDeviceToHost, r->st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(r->st);
+      if (e != cudaSuccess) {
+        cudaFreeHost(pinned);
+        return cuda_fail(e, "qt_expectation");
+      }
+      for (int m = 0; m < nm; ++m) out[static_cast<size_t>(t) * M + g0 + m] = pinned[1 + m] / pinned[0];
+    }
+  cudaFreeHost(pinned);
+  return QT_OK;
+}
+
+qt_status qt_run_state(const qt_run* r, uint32_t t, void* dst, size_t bytes) {
+  clear_error();
+  if (!r || !dst) return set_error(QT_ERR_INVALID_ARG, "qt_run_state: NULL argument");
+  if (r->states.empty()) return set_error(QT_ERR_INVALID_ARG, "qt_run_state: run did not keep its states");
+  if (t >= r->T) return set_error(QT_ERR_INVALID_ARG, "qt_run_state: trajectory %u out of range", t);
+  const size_t sb = sizeof(float2) << r->n;
+  if (bytes < sb) return set_error(QT_ERR_INVALID_ARG, "qt_run_state: %zu bytes < %zu", bytes, sb);
+  DevBuf tmp;
+  if (!tmp.alloc(sb, r->st)) return set_error(QT_ERR_OUT_OF_MEMORY, "qt_run_state: buffer");
+  QT_CUDA(cudaMemcpyAsync(tmp.p, r->states[t].p, sb, cudaMemcpyDeviceToDevice, r->st), "cudaMemcpyAsync");
+  const double N = r->norms[t];
+  QT_CUDA(launch_scale(tmp.as<float2>(), static_cast<int>(r->n), static_cast<float>(1.0 / std::sqrt(N)), r->st),
+          "scale kernel launch");
+  QT_CUDA(cudaMemcpyAsync(dst, tmp.p, sb, cudaMemcpyDeviceToHost, r->st), "cudaMemcpyAsync");
+  QT_CUDA(cudaStreamSynchronize(r->st), "cudaStreamSynchronize");
+  return QT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// state-level calls
+// ---------------------------------------------------------------------------
+static qt_status check_state(const void* state, uint32_t n, const char* who) {
+  if (!state) return set_error(QT_ERR_INVALID_ARG, "%s: state is NULL", who);
+  if (reinterpret_cast<uintptr_t>(state) & 15u) return set_error(QT_ERR_INVALID_ARG, "%s: state not 16-byte aligned", who);
+  if (n < 1 || n > QT_MAX_QUBITS) return set_error(QT_ERR_INVALID_ARG, "%s: n=%u outside 1..%d", who, n, QT_MAX_QUBITS);
+  return QT_OK;
+}
+
+static qt_status check_qubits(uint32_t n, uint32_t q, const uint32_t* qubits, const char* who) {
+  if (!qubits) return set_error(QT_ERR_INVALID_ARG, "%s: qubits is NULL", who);
+  uint64_t m = 0;
+  for (uint32_t b = 0; b < q; ++b) {
+    if (qubits[b] >= n) return set_error(QT_ERR_INVALID_ARG, "%s: qubit %u >= n", who, qubits[b]);
+    if (m & (1ull << qubits[b])) return set_error(QT_ERR_INVALID_ARG, "%s: repeated qubit", who);
+    m |= 1ull << qubits[b];
+  }
+  return QT_OK;
+}
+
+qt_status qt_state_apply(void* state, uint32_t n, uint32_t q, const uint32_t* qubits, const double* U,
+                         uint32_t precision, void* stream) {
+  clear_error();
+  qt_status s = check_state(state, n, "qt_state_apply");
+  if (s != QT_OK) return s;
+  if (q < 1 || q > n || q > 5) return set_error(QT_ERR_UNSUPPORTED, "qt_state_apply: q=%u (1..min(n,5))", q);
+  if (precision != QT_FP32 && precision != QT_TF32X3) return set_error(QT_ERR_INVALID_ARG, "qt_state_apply: precision");
+  if (!U) return set_error(QT_ERR_INVALID_ARG, "qt_state_apply: U is NULL");
+  s = check_qubits(n, q, qubits, "qt_state_apply");
+  if (s != QT_OK) return s;
+  // reorder the matrix basis to ascending qubits
+  std::vector<uint32_t> sorted(qubits, qubits + q);
+  std::sort(sorted.begin(), sorted.end());
+  int pos[QT_MAX_OP_QUBITS];
+  for (uint32_t b = 0; b < q; ++b)
+    pos[b] = static_cast<int>(std::lower_bound(sorted.begin(), sorted.end(), qubits[b]) - sorted.begin());
+  const int D = 1 << q;
+  auto perm = [&](int i) {   // user-basis index of sorted-basis index i
+    int u = 0;
+    for (uint32_t b = 0; b < q; ++b)
+      if ((i >> pos[b]) & 1) u |= 1 << b;
+    return u;
+  };
+  std::vector<float2> M(static_cast<size_t>(D) * D);
+  for (int i = 0; i < D; ++i)
+    for (int j = 0; j < D; ++j) {
+      const size_t e = static_cast<size_t>(perm(i)) * D + perm(j);
+      M[static_cast<size_t>(i) * D + j] = make_float2(static_cast<float>(U[2 * e]), static_cast<float>(U[2 * e + 1]));
+    }
+  QT_CUDA(launch_apply(static_cast<float2*>(state), static_cast<int>(n), static_cast<int>(q), sorted.data(), M.data(),
+                       static_cast<cudaStream_t>(stream)),
+          "qt_state_apply");
+  return QT_OK;
+}
+
+qt_status qt_state_reduced_density(const void* state, uint32_t n, uint32_t q, const uint32_t* qubits, double* out,
+                                   void* stream) {
+  clear_error();
+  qt_status s = check_state(state, n, "qt_state_reduced_density");
+  if (s != QT_OK) return s;
+  if (q < 1 || q > n || q > static_cast<uint32_t>(kRdmMaxQ))
+    return set_error(QT_ERR_UNSUPPORTED, "qt_state_reduced_density: q=%u (1..min(n,3))", q);
+  if (!out) return set_error(QT_ERR_INVALID_ARG, "qt_state_reduced_density: out is NULL");
+  s = check_qubits(n, q, qubits, "qt_state_reduced_density");
+  if (s != QT_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ScratchBufs scr;
+  if (!scr.alloc(1, st)) return set_error(QT_ERR_OUT_OF_MEMORY, "qt_state_reduced_density: scratch");
+  QT_CUDA(launch_rdm(static_cast<const float2*>(state), static_cast<int>(n), static_cast<int>(q), qubits, scr.s, st),
+          "qt_state_reduced_density");
+  double r[64];
+  QT_CUDA(cudaMemcpyAsync(r, scr.s.result, sizeof(double) << (2 * q), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+  QT_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+  rdm_unpack(static_cast<int>(q), r, out);
+  return QT_OK;
+}
+
+qt_status qt_state_sample(const void* state, uint32_t n, uint64_t seed, uint64_t traj, uint32_t S, uint64_t* out,
+                          void* stream) {
+  clear_error();
+  qt_status s = check_state(state, n, "qt_state_sample");
+  if (s != QT_OK) return s;
+  if (S && !out) return set_error(QT_ERR_INVALID_ARG, "qt_state_sample: out is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ScratchBufs scr;
+  DevBuf d;
+  if (!scr.alloc(static_cast<int>(n), st) || (S && !d.alloc(sizeof(uint64_t) * S, st)))
+    return set_error(QT_ERR_OUT_OF_MEMORY, "qt_state_sample: scratch");
+  QT_CUDA(launch_sample(static_cast<const float2*>(state), static_cast<int>(n), seed, traj, S, d.as<uint64_t>(), scr.s, st),
+          "qt_state_sample");
+  if (S) QT_CUDA(cudaMemcpyAsync(out, d.p, sizeof(uint64_t) * S, cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+  QT_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+  return QT_OK;
+}
+
+qt_status qt_state_expect_z(const void* state, uint32_t n, uint32_t M, const uint64_t* masks, double* out,
+                            void* stream) {
+  clear_error();
+  qt_status s = check_state(state, n, "qt_state_expect_z");
+  if (s != QT_OK) return s;
+  if (M && (!masks || !out)) return set_error(QT_ERR_INVALID_ARG, "qt_state_expect_z: NULL argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ScratchBufs scr;
+  if (!scr.alloc(1, st)) return set_error(QT_ERR_OUT_OF_MEMORY, "qt_state_expect_z: scratch");
+  double r[kExpGroup + 1];
+  for (uint32_t g0 = 0; g0 < M; g0 += kExpGroup) {
+    const int nm = static_cast<int>(std::min<uint32_t>(kExpGroup, M - g0));
+    QT_CUDA(launch_expect(static_cast<const float2*>(state), static_cast<int>(n), nm, masks + g0, scr.s, st),
+            "qt_state_expect_z");
+    QT_CUDA(cudaMemcpyAsync(r, scr.s.result, sizeof(r), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+    QT_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    for (int m = 0; m < nm; ++m) out[g0 + m] = r[1 + m] / r[0];
+  }
+  return QT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,85 @@
+"""Micro-benchmark of the fused-gate kernel (Alg. 1) and the read passes.
+
+Times each kernel through the C ABI's state-level calls on a device state
+of 2^n complex64 amplitudes, with CUDA events on the launching stream after
+warm-up, and reports achieved bandwidth against the algorithmic bytes:
+16 * 2^n per fused-gate pass (read + write), 8 * 2^n per read pass.
+
+    python -m paper_2111_02396_gb300.kernel_bench --n 30 --k 4
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+import numpy as np
+
+PATTERNS = {
+    "high": lambda n, k: list(range(n - k, n)),
+    "mid": lambda n, k: [n // 2 + 2 * j for j in range(k)],
+    "low0": lambda n, k: list(range(k)),
+    "low1": lambda n, k: list(range(1, k + 1)),
+    "mixed": lambda n, k: [0] + list(range(n - k + 1, n)),
+    "spread": lambda n, k: [int(round(j * (n - 1) / max(k - 1, 1))) for j in range(k)],
+}
+
+
+def main(argv=None):
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import torch
+
+    import paper_2111_02396_gb300 as pkg
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=28)
+    ap.add_argument("--k", type=int, nargs="+", default=[1, 2, 3, 4, 5])
+    ap.add_argument("--patterns", nargs="+", default=list(PATTERNS))
+    ap.add_argument("--reps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--reads", action="store_true", help="also time the read passes")
+    args = ap.parse_args(argv)
+    pkg.load()
+    n = args.n
+    st = torch.cuda.current_stream()
+    d = torch.zeros(1 << n, dtype=torch.complex64, device="cuda")
+    d[0] = 1
+    rng = np.random.default_rng(0)
+    rows = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timeit(fn, nbytes):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(args.reps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.reps
+        return ms, nbytes / (ms / 1e3) / 1e9
+
+    for k in args.k:
+        q, _ = np.linalg.qr(rng.normal(size=(1 << k, 1 << k)) + 1j * rng.normal(size=(1 << k, 1 << k)))
+        for pat in args.patterns:
+            qubits = PATTERNS[pat](n, k)
+            ms, gbs = timeit(lambda: pkg.qt_state_apply(d.data_ptr(), n, qubits, q,
+                                                        stream=st.cuda_stream), 16 << n)
+            rows.append(dict(kernel="apply", n=n, k=k, pattern=pat, qubits=qubits, ms=ms, gbs=gbs))
+            print(json.dumps(rows[-1]), flush=True)
+    if args.reads:
+        for q in (1, 2):
+            ms, gbs = timeit(lambda: pkg.qt_state_reduced_density(d.data_ptr(), n, list(range(n - q, n)),
+                                                                  stream=st.cuda_stream), 8 << n)
+            print(json.dumps(dict(kernel="rdm", n=n, q=q, ms=ms, gbs=gbs)), flush=True)
+        masks = [1 << j for j in range(min(n, 16))]
+        ms, gbs = timeit(lambda: pkg.qt_state_expect_z(d.data_ptr(), n, masks, stream=st.cuda_stream), 8 << n)
+        print(json.dumps(dict(kernel="expect16", n=n, ms=ms, gbs=gbs)), flush=True)
+        ms, gbs = timeit(lambda: pkg.qt_state_sample(d.data_ptr(), n, 0, 0, 100, stream=st.cuda_stream), 8 << n)
+        print(json.dumps(dict(kernel="sample100", n=n, ms=ms, gbs=gbs)), flush=True)
+
+
+if __name__ == "__main__":
+    main()

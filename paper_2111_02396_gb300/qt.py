@@ -1,0 +1,341 @@
+"""ctypes binding of libqt.so: the C ABI of include/qt.h under the same names.
+
+Argument marshalling only -- every step of the trajectory path runs in the
+library's CUDA kernels.  There is no fallback: if libqt.so cannot be loaded
+the import fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+QT_OK = 0
+QT_ERR_INVALID_ARG = -1
+QT_ERR_NOT_CPTP = -2
+QT_ERR_OUT_OF_MEMORY = -3
+QT_ERR_CUDA = -4
+QT_ERR_TIMEOUT = -5
+QT_ERR_UNSUPPORTED = -6
+QT_ERR_INTERNAL = -7
+
+QT_OP_GATE, QT_OP_KRAUS, QT_OP_MIXTURE = 0, 1, 2
+QT_DELAYED, QT_EAGER = 0, 1
+QT_FP32, QT_TF32X3 = 0, 1
+QT_FLAG_TIME_KERNELS = 1
+
+
+class QtError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"qt status {status}: {msg}")
+        self.status = status
+
+
+class qt_op(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("moment", C.c_uint32), ("num_qubits", C.c_uint32),
+                ("qubits", C.c_uint32 * 6), ("num_ops", C.c_uint32),
+                ("probs", C.c_void_p), ("mats", C.c_void_p)]
+
+
+class qt_run_params(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("first_traj", C.c_uint64), ("num_traj", C.c_uint32),
+                ("mode", C.c_uint32), ("precision", C.c_uint32), ("samples_per_traj", C.c_uint32),
+                ("num_z_masks", C.c_uint32), ("z_masks", C.c_void_p), ("keep_states", C.c_uint32),
+                ("flags", C.c_uint32), ("stream", C.c_void_p), ("timeout_ns", C.c_uint64)]
+
+
+class qt_run_stats_t(C.Structure):
+    _fields_ = [("num_traj", C.c_uint32), ("num_channels", C.c_uint32),
+                ("fused_passes", C.c_uint64), ("prob_passes", C.c_uint64),
+                ("gate_ops", C.c_uint64), ("flushes", C.c_uint64),
+                ("device_ms", C.c_double), ("apply_ms", C.c_double),
+                ("apply_bytes", C.c_uint64), ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64),
+                ("kernel_launches", C.c_uint64)]
+
+
+class qt_fused_info_t(C.Structure):
+    _fields_ = [("num_fused", C.c_uint32), ("max_width", C.c_uint32),
+                ("num_ops", C.c_uint32), ("num_channels", C.c_uint32)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+# every exported symbol of include/qt.h
+EXPORTS = [
+    "qt_circuit_create", "qt_fuse", "qt_run_trajectories", "qt_sample", "qt_expectation",
+    "qt_run_kraus_indices", "qt_run_stats", "qt_run_state", "qt_set_allocator",
+    "qt_circuit_destroy", "qt_fused_destroy", "qt_run_destroy", "qt_last_error",
+    "qt_fused_info", "qt_fused_gate", "qt_channel_lower_bounds",
+    "qt_state_apply", "qt_state_reduced_density", "qt_state_sample", "qt_state_expect_z",
+]
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libqt.so (building it first if needed).  Raises if it cannot."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"libqt.so missing at {_build.LIB}: the CUDA library is required")
+        lib = C.CDLL(_build.LIB)
+        P = C.c_void_p
+        u32, u64 = C.c_uint32, C.c_uint64
+        sig = {
+            "qt_circuit_create": [u32, u32, P, P],
+            "qt_fuse": [P, u32, P],
+            "qt_run_trajectories": [P, P, P],
+            "qt_sample": [P, u32, P],
+            "qt_expectation": [P, u32, P, P],
+            "qt_run_kraus_indices": [P, P, P, C.c_size_t],
+            "qt_run_stats": [P, P],
+            "qt_run_state": [P, u32, P, C.c_size_t],
+            "qt_set_allocator": [P, P, P],
+            "qt_fused_info": [P, P],
+            "qt_fused_gate": [P, u32, P, P, P, P, C.c_size_t, P],
+            "qt_channel_lower_bounds": [P, u32, P, C.c_size_t, P],
+            "qt_state_apply": [P, u32, u32, P, P, u32, P],
+            "qt_state_reduced_density": [P, u32, u32, P, P, P],
+            "qt_state_sample": [P, u32, u64, u64, u32, P, P],
+            "qt_state_expect_z": [P, u32, u32, P, P, P],
+        }
+        for name, args in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = C.c_int
+        for name in ("qt_circuit_destroy", "qt_fused_destroy", "qt_run_destroy"):
+            fn = getattr(lib, name)
+            fn.argtypes = [P]
+            fn.restype = None
+        lib.qt_last_error.restype = C.c_char_p
+        lib.qt_last_error.argtypes = []
+        _lib = lib
+        return lib
+
+
+def _check(status):
+    if status != QT_OK:
+        msg = load().qt_last_error().decode(errors="replace")
+        raise QtError(status, msg)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+# ----------------------------------------------------------------------------
+# torch plumbing: device memory from torch's caching allocator, torch streams
+# ----------------------------------------------------------------------------
+_alloc_refs = None
+
+
+def use_torch_allocator(enable: bool = True):
+    """Route the library's device allocations through torch's caching allocator."""
+    global _alloc_refs
+    lib = load()
+    if not enable:
+        _check(lib.qt_set_allocator(None, None, None))
+        _alloc_refs = None
+        return
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                      stream or 0)
+        except Exception:  # noqa: BLE001 -- reported to the library as NULL
+            return None
+
+    def _free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a, f = ALLOC_FN(_alloc), FREE_FN(_free)
+    _alloc_refs = (a, f)
+    _check(lib.qt_set_allocator(C.cast(a, C.c_void_p), C.cast(f, C.c_void_p), None))
+
+
+def current_stream_handle():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+# ----------------------------------------------------------------------------
+# handles
+# ----------------------------------------------------------------------------
+class Circuit:
+    """qt_circuit built from a list of ops (qtsynth.Op-like objects)."""
+
+    def __init__(self, num_qubits, ops):
+        lib = load()
+        self.num_qubits = int(num_qubits)
+        arr = (qt_op * max(len(ops), 1))()
+        self._keep = []
+        for i, o in enumerate(ops):
+            mats = np.ascontiguousarray(np.asarray(o.mats, dtype=np.complex128)).view(np.float64).ravel()
+            self._keep.append(mats)
+            arr[i].kind = int(o.kind)
+            arr[i].moment = int(o.moment)
+            arr[i].num_qubits = len(o.qubits)
+            for b, q in enumerate(o.qubits):
+                arr[i].qubits[b] = int(q)
+            arr[i].num_ops = int(np.asarray(o.mats).shape[0])
+            arr[i].mats = mats.ctypes.data
+            if o.probs is not None:
+                pr = np.ascontiguousarray(o.probs, dtype=np.float64)
+                self._keep.append(pr)
+                arr[i].probs = pr.ctypes.data
+        self.h = C.c_void_p()
+        _check(lib.qt_circuit_create(self.num_qubits, len(ops), C.cast(arr, C.c_void_p), C.byref(self.h)))
+        self.num_channels = sum(1 for o in ops if o.kind != QT_OP_GATE)
+        self.num_ops = len(ops)
+        self._keep = None
+
+    @classmethod
+    def from_synth(cls, circ):
+        return cls(circ.num_qubits, circ.ops)
+
+    def lower_bounds(self, channel):
+        lib = load()
+        out = np.zeros(64)
+        k = C.c_uint32()
+        _check(lib.qt_channel_lower_bounds(self.h, channel, _ptr(out), 64, C.byref(k)))
+        return out[:k.value].copy()
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.qt_circuit_destroy(self.h)
+            self.h = None
+
+
+class Fused:
+    def __init__(self, circuit: Circuit, max_fused_qubits: int = 0):
+        lib = load()
+        self.circuit = circuit           # the circuit must outlive the fused handle
+        self.h = C.c_void_p()
+        _check(lib.qt_fuse(circuit.h, int(max_fused_qubits), C.byref(self.h)))
+
+    def info(self):
+        i = qt_fused_info_t()
+        _check(load().qt_fused_info(self.h, C.byref(i)))
+        return dict(num_fused=i.num_fused, max_width=i.max_width, num_ops=i.num_ops,
+                    num_channels=i.num_channels)
+
+    def gate(self, g):
+        lib = load()
+        w = C.c_uint32()
+        tg = np.zeros(8, dtype=np.uint32)
+        nm = C.c_uint32()
+        _check(lib.qt_fused_gate(self.h, g, C.byref(w), _ptr(tg), C.byref(nm), None, 0, None))
+        mem = np.zeros(max(nm.value, 1), dtype=np.uint32)
+        mat = np.zeros((1 << w.value) ** 2, dtype=np.complex128)
+        _check(lib.qt_fused_gate(self.h, g, None, None, None, _ptr(mem), len(mem), _ptr(mat)))
+        D = 1 << w.value
+        return dict(targets=tg[:w.value].copy(), members=mem[:nm.value].copy(),
+                    matrix=mat.reshape(D, D))
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.qt_fused_destroy(self.h)
+            self.h = None
+
+
+class Run:
+    def __init__(self, fused: Fused, num_traj, *, seed=0, first_traj=0, mode=QT_DELAYED,
+                 precision=QT_FP32, samples_per_traj=0, z_masks=(), keep_states=False,
+                 time_kernels=False, stream=None):
+        lib = load()
+        self.fused = fused
+        self.masks = np.ascontiguousarray(np.asarray(z_masks, dtype=np.uint64))
+        p = qt_run_params()
+        p.seed, p.first_traj, p.num_traj = seed, first_traj, num_traj
+        p.mode, p.precision, p.samples_per_traj = mode, precision, samples_per_traj
+        p.num_z_masks = len(self.masks)
+        p.z_masks = self.masks.ctypes.data if len(self.masks) else None
+        p.keep_states = 1 if keep_states else 0
+        p.flags = QT_FLAG_TIME_KERNELS if time_kernels else 0
+        p.stream = stream
+        self.params = p
+        self.num_traj = num_traj
+        self.S = samples_per_traj
+        self.h = C.c_void_p()
+        _check(lib.qt_run_trajectories(fused.h, C.byref(p), C.byref(self.h)))
+
+    def samples(self, S=None):
+        S = self.S if S is None else S
+        out = np.zeros(max(self.num_traj * S, 1), dtype=np.uint64)
+        _check(load().qt_sample(self.h, S, _ptr(out)))
+        return out[:self.num_traj * S].reshape(self.num_traj, S)
+
+    def expectation(self, masks=None):
+        m = self.masks if masks is None else np.ascontiguousarray(np.asarray(masks, dtype=np.uint64))
+        out = np.zeros(max(self.num_traj * len(m), 1))
+        _check(load().qt_expectation(self.h, len(m), _ptr(m) if len(m) else None, _ptr(out)))
+        return out[:self.num_traj * len(m)].reshape(self.num_traj, len(m))
+
+    def kraus_indices(self):
+        nch = self.fused.circuit.num_channels
+        k = np.zeros(max(self.num_traj * nch, 1), dtype=np.int32)
+        s = np.zeros_like(k)
+        _check(load().qt_run_kraus_indices(self.h, _ptr(k), _ptr(s), len(k)))
+        n = self.num_traj * nch
+        return k[:n].reshape(self.num_traj, nch), s[:n].reshape(self.num_traj, nch)
+
+    def stats(self):
+        s = qt_run_stats_t()
+        _check(load().qt_run_stats(self.h, C.byref(s)))
+        return {f: getattr(s, f) for f, _ in qt_run_stats_t._fields_}
+
+    def state(self, t):
+        n = self.fused.circuit.num_qubits
+        out = np.zeros(1 << n, dtype=np.complex64)
+        _check(load().qt_run_state(self.h, t, _ptr(out), out.nbytes))
+        return out
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.qt_run_destroy(self.h)
+            self.h = None
+
+
+# ----------------------------------------------------------------------------
+# state-level calls on a device pointer (e.g. a torch tensor's data_ptr())
+# ----------------------------------------------------------------------------
+def qt_state_apply(state_ptr, n, qubits, U, precision=QT_FP32, stream=None):
+    q = np.ascontiguousarray(qubits, dtype=np.uint32)
+    Um = np.ascontiguousarray(np.asarray(U, dtype=np.complex128)).view(np.float64)
+    _check(load().qt_state_apply(state_ptr, n, len(q), _ptr(q), _ptr(Um), precision, stream))
+
+
+def qt_state_reduced_density(state_ptr, n, qubits, stream=None):
+    q = np.ascontiguousarray(qubits, dtype=np.uint32)
+    D = 1 << len(q)
+    out = np.zeros(D * D, dtype=np.complex128)
+    _check(load().qt_state_reduced_density(state_ptr, n, len(q), _ptr(q), _ptr(out), stream))
+    return out.reshape(D, D)
+
+
+def qt_state_sample(state_ptr, n, seed, traj, S, stream=None):
+    out = np.zeros(max(S, 1), dtype=np.uint64)
+    _check(load().qt_state_sample(state_ptr, n, seed, traj, S, _ptr(out), stream))
+    return out[:S]
+
+
+def qt_state_expect_z(state_ptr, n, masks, stream=None):
+    m = np.ascontiguousarray(masks, dtype=np.uint64)
+    out = np.zeros(max(len(m), 1))
+    _check(load().qt_state_expect_z(state_ptr, n, len(m), _ptr(m), _ptr(out), stream))
+    return out[:len(m)]

@@ -417,4 +417,7 @@ def random_noisy_circuit(n, num_ops, seed, *, max_gate_qubits=3, noise=0.05,
             q = int(rng.integers(1, min(max_gate_qubits, n) + 1))
             qs = tuple(int(x) for x in rng.choice(n, q, replace=False))
             c.gate(random_unitary(2 ** q, rng), qs, place(qs))
+    # a circuit is a sequence of moments: list ops moment by moment (stable,
+    # so ops sharing a qubit keep their order)
+    c.ops.sort(key=lambda o: o.moment)
     return c

@@ -1,0 +1,142 @@
+"""GPU checks at the full 30-qubit size, in the benchmark's launch configuration.
+
+The FP64 oracle cannot run the whole 30-qubit workload in a test, so these
+checks use outputs it can compute one by one, or properties that hold at
+any size:
+  * one fused 4-qubit gate on a seeded 2^30 state: sampled output
+    amplitudes against the oracle applied to their 16-amplitude gather set;
+  * a 30-qubit circuit made of six independent 5-qubit blocks (qubits
+    interleaved across the index bits, fused to 4 qubits by the library):
+    sampled amplitudes against the product of the six block states from
+    the oracle;
+  * the 30-qubit 5x6 grid workload with damping: every stage-1 branch
+    record equals the decision the oracle's own Philox draws and lower
+    bounds give; flushes happen exactly where stage 1 cannot decide; the
+    sampled bitstrings' per-qubit frequencies agree with <Z_j> of the same
+    final states.
+"""
+import numpy as np
+import pytest
+
+import qtsynth as qs
+from gpu_util import KERNEL_L2, STATE_L2, torch_cuda
+
+pytestmark = pytest.mark.gpu
+N = 30
+
+
+@pytest.fixture(scope="module")
+def qt():
+    import paper_2111_02396_gb300 as pkg
+    pkg.load()
+    torch_cuda()
+    return pkg
+
+
+def test_single_gate_sampled_outputs(qt, orc):
+    torch = torch_cuda()
+    g = torch.Generator(device="cuda").manual_seed(1234)
+    d = torch.randn(2 << N, device="cuda", generator=g, dtype=torch.float32).view(torch.complex64)
+    rng = np.random.default_rng(3)
+    xs = rng.integers(0, 1 << N, 3000)
+    for qubits in ([29, 3, 17, 8], [0, 1, 2, 3], [0, 29, 28, 14], [5, 6, 7, 8]):
+        U = qs.random_unitary(16, rng)
+        before = d.clone()
+        qt.qt_state_apply(d.data_ptr(), N, qubits, U)
+        mask = sum(1 << q for q in qubits)
+        idx = []
+        for x in xs:
+            base = int(x) & ~mask
+            idx.append([base | sum(((m >> b) & 1) << q for b, q in enumerate(qubits))
+                        for m in range(16)])
+        idx = torch.tensor(np.array(idx), device="cuda")
+        vin = before[idx].cpu().numpy().astype(np.complex128)          # [S, 16] gather sets
+        vout = d[idx].cpu().numpy().astype(np.complex128)
+        want = np.stack([orc.apply(v.copy(), [0, 1, 2, 3], U) for v in vin])
+        err = np.linalg.norm(vout - want) / np.linalg.norm(want)
+        assert err < KERNEL_L2, (qubits, err)
+        del before
+
+
+def block_circuit(seed=0, blocks=6, width=5, depth=12):
+    """Independent 5-qubit random circuits on qubits {b, b+6, b+12, ...}."""
+    rng = np.random.default_rng([0x99, seed])
+    n = blocks * width
+    c = qs.Circuit(n)
+    sub = []
+    for b in range(blocks):
+        qs_b = [b + blocks * j for j in range(width)]
+        s = qs.Circuit(width)
+        for layer in range(depth):
+            for j in range(width):
+                s.gate(qs.random_unitary(2, rng), (j,), 2 * layer)
+            for j in range(layer % 2, width - 1, 2):
+                s.gate(qs.CZ, (j, j + 1), 2 * layer + 1)
+        sub.append((qs_b, s))
+    m = 0
+    for layer_ops in range(max(len(s.ops) for _, s in sub)):
+        for qs_b, s in sub:
+            if layer_ops < len(s.ops):
+                o = s.ops[layer_ops]
+                c.gate(o.mats[0], tuple(qs_b[j] for j in o.qubits), m)
+        m += 1
+    return c, sub
+
+
+def test_block_product_circuit_sampled_amplitudes(qt, orc):
+    circ, sub = block_circuit()
+    qc = qt.Circuit.from_synth(circ)
+    run = qt.Run(qt.Fused(qc, 4), 1, keep_states=True, samples_per_traj=2000)
+    psi = run.state(0)
+    states = [(qs_b, orc.run_trajectory(s)["state"]) for qs_b, s in sub]
+    rng = np.random.default_rng(1)
+    # uniform indices plus sampled ones (drawn from |psi|^2: the large amplitudes)
+    xs = np.concatenate([rng.integers(0, 1 << N, 20000), run.samples()[0].astype(np.int64)])
+    want = np.ones(len(xs), dtype=np.complex128)
+    for qs_b, st in states:
+        loc = np.zeros(len(xs), dtype=np.int64)
+        for j, q in enumerate(qs_b):
+            loc |= ((xs >> q) & 1) << j
+        want *= st[loc]
+    got = psi[xs].astype(np.complex128)
+    # relative L2 over the sample, scaled by the state's norm density
+    err = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert err < STATE_L2, err
+
+
+def test_grid30_branch_records_and_marginals(qt, orc):
+    circ = qs.config1_circuit()
+    qc = qt.Circuit.from_synth(circ)
+    f = qt.Fused(qc, 4)
+    T, S = 2, 4000
+    masks = [1 << j for j in range(N)]
+    run = qt.Run(f, T, seed=0, samples_per_traj=S, z_masks=masks)
+    kr, st = run.kraus_indices()
+    # stage-1 decisions from the oracle's draws and lower bounds
+    chans = [o for o in circ.ops if o.kind != qs.KIND_GATE]
+    lbs = [[orc.lower_bound(K) for K in o.mats] for o in chans[:2]]   # AD and PD types
+    lb_by_kind = {}
+    for o in chans:
+        key = (o.mats.shape[0], o.mats[1, 0, 1] != 0)   # AD has an off-diagonal K1
+        if key not in lb_by_kind:
+            lb_by_kind[key] = [orc.lower_bound(K) for K in o.mats]
+    flushes = 0
+    for t in range(T):
+        for ch, o in enumerate(chans):
+            lb = lb_by_kind[(o.mats.shape[0], o.mats[1, 0, 1] != 0)]
+            r = orc.u01(0, t, 0, ch)
+            if r < lb[0]:
+                assert kr[t, ch] == 0 and st[t, ch] == 1
+            else:
+                assert st[t, ch] == 2
+                flushes += 1
+    assert run.stats()["flushes"] == flushes
+    # sampled marginals vs <Z_j> of the same states
+    smp = run.samples()
+    z = run.expectation()
+    for t in range(T):
+        bits = ((smp[t][:, None] >> np.arange(N, dtype=np.uint64)[None, :]) & np.uint64(1)).astype(np.float64)
+        p1 = (1 - z[t]) / 2
+        se = np.sqrt(np.maximum(p1 * (1 - p1), 1e-4) / S)
+        assert np.all(np.abs(bits.mean(0) - p1) < 5 * se)
+    assert lbs  # lower bounds were evaluated by the oracle

@@ -1,0 +1,146 @@
+"""GPU parity of the hot kernels through the C ABI's state-level calls.
+
+Each test puts a seeded complex64 state in device memory, calls the kernel
+through libqt.so and compares with the FP64 oracle on the same input:
+fused-gate application (Alg. 1) for every width 1..5 and target pattern
+(all low qubits, all high, qubit 0 in or out, unsorted), the reduced
+density block behind P_i = <psi|K_i^dag K_i|psi> (Alg. 2 step 14),
+Z expectations and bitstring sampling.
+"""
+import numpy as np
+import pytest
+
+import qtsynth as qs
+from gpu_util import (KERNEL_L2, MARGIN, STATE_L2, random_state, rel_l2, to_device,
+                      torch_cuda)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qt():
+    import paper_2111_02396_gb300 as pkg
+    pkg.load()
+    torch_cuda()
+    return pkg
+
+
+def patterns(n, k, rng):
+    yield list(range(k))                                  # all low, includes qubit 0
+    yield list(range(n - k, n))                           # all high
+    yield [0] + list(range(n - k + 1, n))                 # qubit 0 + high
+    yield list(range(1, k + 1))                           # low, qubit 0 free
+    yield [int(x) for x in rng.choice(n, k, replace=False)]   # random, unsorted
+    yield [int(x) for x in rng.choice(np.arange(1, n), k, replace=False)]
+
+
+@pytest.mark.parametrize("n", [5, 11, 17])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+def test_apply_every_pattern(qt, orc, n, k):
+    if k > n:
+        pytest.skip("k > n")
+    rng = np.random.default_rng([n, k])
+    for qubits in patterns(n, k, rng):
+        U = qs.random_unitary(1 << k, rng)
+        psi = random_state(n, k)
+        d = to_device(psi)
+        qt.qt_state_apply(d.data_ptr(), n, qubits, U)
+        got = d.cpu().numpy()
+        want = orc.apply(psi.astype(np.complex128), qubits, U)
+        assert rel_l2(got, want) < KERNEL_L2, (qubits, rel_l2(got, want))
+
+
+def test_apply_sequence_ragged_sizes(qt, orc):
+    """Many gates in sequence on sizes that span several grid waves and a
+    one-set edge case (n == k)."""
+    for n in (4, 9, 20, 23):
+        rng = np.random.default_rng(n)
+        psi = random_state(n, 3)
+        d = to_device(psi)
+        ref = psi.astype(np.complex128)
+        for _ in range(30):
+            k = int(rng.integers(1, min(5, n) + 1))
+            qubits = [int(x) for x in rng.choice(n, k, replace=False)]
+            U = qs.random_unitary(1 << k, rng)
+            qt.qt_state_apply(d.data_ptr(), n, qubits, U)
+            orc.apply(ref, qubits, U)
+        assert rel_l2(d.cpu().numpy(), ref) < STATE_L2
+
+
+def test_apply_non_unitary_and_n_equals_k(qt, orc):
+    rng = np.random.default_rng(9)
+    for n in (1, 2, 3):
+        psi = random_state(n, 1)
+        d = to_device(psi)
+        A = rng.normal(size=(1 << n, 1 << n)) + 1j * rng.normal(size=(1 << n, 1 << n))
+        qt.qt_state_apply(d.data_ptr(), n, list(range(n))[::-1], A)
+        want = orc.apply(psi.astype(np.complex128), list(range(n))[::-1], A)
+        assert rel_l2(d.cpu().numpy(), want) < KERNEL_L2
+
+
+@pytest.mark.parametrize("n,q", [(3, 1), (12, 1), (16, 2), (18, 3), (21, 2)])
+def test_probabilities_from_reduced_density(qt, orc, n, q):
+    rng = np.random.default_rng([n, q])
+    psi = random_state(n, 5)
+    d = to_device(psi)
+    for _ in range(3):
+        qubits = [int(x) for x in rng.choice(n, q, replace=False)]
+        rho = qt.qt_state_reduced_density(d.data_ptr(), n, qubits)
+        Ks = qs.circuits.random_kraus(1 << q, 3, rng)
+        P_gpu = np.array([np.trace(K.conj().T @ K @ rho).real for K in Ks])
+        P_orc = orc.kraus_norms(psi.astype(np.complex128), qubits, Ks)
+        np.testing.assert_allclose(P_gpu, P_orc, rtol=1e-6, atol=1e-9)
+        assert abs(np.trace(rho).real - orc.norm2(psi.astype(np.complex128))) < 1e-6
+
+
+@pytest.mark.parametrize("n", [1, 6, 15, 22])
+def test_expect_z(qt, orc, n):
+    psi = random_state(n, 7) * np.float32(1.3)
+    d = to_device(psi)
+    rng = np.random.default_rng(n)
+    masks = [1 << j for j in range(n)] + [int(x) for x in rng.integers(0, 1 << n, 20)]
+    got = qt.qt_state_expect_z(d.data_ptr(), n, masks)
+    want = orc.expect_z(psi.astype(np.complex128), masks)
+    np.testing.assert_allclose(got, want, atol=2e-6)
+
+
+@pytest.mark.parametrize("n,S", [(1, 50), (4, 300), (11, 3000), (16, 3000), (20, 1000)])
+def test_sample_parity(qt, orc, n, S):
+    psi = random_state(n, 11)
+    d = to_device(psi)
+    got = qt.qt_state_sample(d.data_ptr(), n, 42, 3, S)
+    want, margin = orc.sample(psi.astype(np.complex128), 42, 3, S)
+    ok = margin > MARGIN
+    assert np.all(got < (1 << n))
+    np.testing.assert_array_equal(got[ok], want[ok])
+    if n <= 11:
+        assert ok.mean() > 0.9
+    # ties: the GPU index must sit next to the oracle's (within the CDF
+    # neighbourhood set by float rounding)
+    if (~ok).any():
+        assert np.all(np.abs(got[~ok].astype(np.int64) - want[~ok].astype(np.int64)) <= 64)
+
+
+def test_sample_ghz_full_support(qt, orc):
+    n = 12
+    psi = np.zeros(1 << n, dtype=np.complex64)
+    psi[0] = psi[-1] = np.float32(1 / np.sqrt(2))
+    d = to_device(psi)
+    got = qt.qt_state_sample(d.data_ptr(), n, 1, 0, 4000)
+    assert set(np.unique(got).tolist()) <= {0, (1 << n) - 1}
+    want, _ = orc.sample(psi.astype(np.complex128), 1, 0, 4000)
+    np.testing.assert_array_equal(got, want)
+
+
+def test_state_calls_reject_bad_arguments(qt):
+    from paper_2111_02396_gb300.qt import QtError
+    torch = torch_cuda()
+    d = torch.zeros(64, dtype=torch.complex64, device="cuda")
+    with pytest.raises(QtError):
+        qt.qt_state_apply(d.data_ptr(), 6, [0, 0], np.eye(4))       # repeated qubit
+    with pytest.raises(QtError):
+        qt.qt_state_apply(d.data_ptr(), 6, [6], np.eye(2))          # out of range
+    with pytest.raises(QtError):
+        qt.qt_state_apply(d.data_ptr() + 8, 6, [1], np.eye(2))      # misaligned
+    with pytest.raises(QtError):
+        qt.qt_state_reduced_density(d.data_ptr(), 6, [0, 1, 2, 3])  # q > 3

@@ -1,0 +1,129 @@
+"""GPU parity of whole trajectory runs (Alg. 2 and the conventional algorithm).
+
+For the same circuits, seeds and Philox counters as the FP64 oracle:
+  * Kraus branch records are equal wherever the draw's margin to the
+    nearest partition boundary exceeds 1e-6 (a closer draw is a tie; the
+    rest of that trajectory is then not compared);
+  * final states agree within relative L2 2e-5 and fidelity 1 - 1e-5;
+  * sampled bitstrings are equal where the CDF margin exceeds 1e-6;
+  * expectations agree.
+Covered: the 10-qubit chain workload (64 trajectories x 100 samples), random
+circuits with every channel kind at fusion widths 2..5, delayed and eager
+modes, and a 20-qubit grid with noise strong enough to force flushes.
+"""
+import numpy as np
+import pytest
+
+import qtsynth as qs
+from gpu_util import MARGIN, STATE_FID, STATE_L2, fidelity, rel_l2, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qt():
+    import paper_2111_02396_gb300 as pkg
+    pkg.load()
+    torch_cuda()
+    return pkg
+
+
+def compare_run(qt, orc, circ, T, *, k, mode, seed=0, S=0, masks=(), check_states=True):
+    qc = qt.Circuit.from_synth(circ)
+    f = qt.Fused(qc, k)
+    run = qt.Run(f, T, seed=seed, mode=mode, samples_per_traj=S, z_masks=masks,
+                 keep_states=check_states)
+    kr, st = run.kraus_indices()
+    omode = orc.DELAYED if mode == qt.QT_DELAYED else orc.EAGER
+    ref = orc.run_trajectories(circ, T, mode=omode, seed=seed, keep_states=True)
+    compared = ties = 0
+    samples = run.samples() if S else None
+    expv = run.expectation() if len(masks) else None
+    for t in range(T):
+        tie = False
+        for ch in range(kr.shape[1]):
+            if ref["margin"][t, ch] <= MARGIN:
+                tie = True
+                ties += 1
+                break
+            assert kr[t, ch] == ref["kraus_idx"][t, ch], (t, ch)
+            assert st[t, ch] == ref["stage"][t, ch], (t, ch)
+        if tie:
+            continue
+        compared += 1
+        psi = ref["states"][t]
+        if check_states:
+            g = run.state(t)
+            assert rel_l2(g, psi) <= STATE_L2, (t, rel_l2(g, psi))
+            assert fidelity(g, psi) >= 1 - STATE_FID
+        if S:
+            want, margin = orc.sample(psi, seed, t, S)
+            ok = margin > MARGIN
+            np.testing.assert_array_equal(samples[t][ok], want[ok])
+        if len(masks):
+            np.testing.assert_allclose(expv[t], orc.expect_z(psi, masks), atol=2e-5)
+    assert compared >= 0.75 * T, (compared, ties)
+    return run, ref
+
+
+def test_config0_chain10(qt, orc):
+    circ = qs.config0_circuit()
+    masks = [1 << j for j in range(10)] + [0b1111111111]
+    run, ref = compare_run(qt, orc, circ, 64, k=2, mode=qt.QT_DELAYED, S=100, masks=masks)
+    st = run.stats()
+    assert st["num_traj"] == 64 and st["kernel_launches"] > 0
+
+
+def test_config0_eager_same_branches(qt, orc):
+    circ = qs.config0_circuit()
+    compare_run(qt, orc, circ, 16, k=2, mode=qt.QT_EAGER, S=20)
+
+
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
+@pytest.mark.parametrize("mode", ["delayed", "eager"])
+def test_random_channels(qt, orc, k, mode):
+    m = qt.QT_DELAYED if mode == "delayed" else qt.QT_EAGER
+    for seed in range(3):
+        circ = qs.random_noisy_circuit(9, 70, 100 + seed, max_gate_qubits=3, noise=0.15,
+                                       channel_prob=0.45)
+        compare_run(qt, orc, circ, 12, k=k, mode=m, seed=seed, S=50, masks=[1, 6, 0x1ff])
+
+
+def test_grid20_forced_flushes(qt, orc):
+    circ = qs.config1_circuit(rows=4, cols=5, depth=12, gamma=1e-2, lam=1e-2)
+    run, ref = compare_run(qt, orc, circ, 4, k=4, mode=qt.QT_DELAYED, S=200,
+                           masks=[1 << j for j in range(20)])
+    assert run.stats()["flushes"] > 0
+    assert run.stats()["flushes"] == int(np.sum(ref["stage"] == 2))
+
+
+def test_mixture_only_circuit_never_flushes(qt, orc):
+    circ = qs.config3_circuit(rows=2, cols=5, depth=10, p=0.05)
+    run, _ = compare_run(qt, orc, circ, 8, k=4, mode=qt.QT_DELAYED, S=50)
+    assert run.stats()["flushes"] == 0 and run.stats()["prob_passes"] == 0
+
+
+def test_amplitude_damping_full_reset(qt, orc):
+    c = qs.Circuit(5)
+    for q in range(5):
+        c.gate(qs.SQRT_X, (q,), 0)
+    for q in range(5):
+        c.channel(qs.amplitude_damping(1.0), (q,), 1)
+    qc = qt.Circuit.from_synth(c)
+    run = qt.Run(qt.Fused(qc, 3), 4, keep_states=True, samples_per_traj=10)
+    for t in range(4):
+        assert abs(abs(run.state(t)[0]) - 1) < 1e-6
+    assert np.all(run.samples() == 0)
+
+
+def test_trajectory_ranges_compose(qt):
+    """Counter-based draws: trajectories [0,8) equal [0,4) + [4,8) (replica sharding)."""
+    circ = qs.config1_circuit(rows=3, cols=4, depth=8, gamma=2e-2, lam=2e-2)
+    qc = qt.Circuit.from_synth(circ)
+    f = qt.Fused(qc, 4)
+    a = qt.Run(f, 8, seed=5, samples_per_traj=30)
+    b0 = qt.Run(f, 4, seed=5, first_traj=0, samples_per_traj=30)
+    b1 = qt.Run(f, 4, seed=5, first_traj=4, samples_per_traj=30)
+    np.testing.assert_array_equal(a.samples(), np.concatenate([b0.samples(), b1.samples()]))
+    np.testing.assert_array_equal(a.kraus_indices()[0],
+                                  np.concatenate([b0.kraus_indices()[0], b1.kraus_indices()[0]]))
