@@ -43,7 +43,9 @@ bool grow(std::vector<Work>& g, size_t a, int kmax, uint64_t all_mask, bool allo
       const uint64_t qb = g[b].mask;
       if ((qb & blocked) == 0) {
         const uint64_t un = g[a].mask | qb;
-        if (popc(un) <= kmax) {
+        // an op wider than the fuse size forms its own gate; it still absorbs
+        // gates on a subset of its qubits
+        if (popc(un) <= std::max(kmax, popc(g[a].mask))) {
           if ((qb & ~g[a].mask) == 0) {      // no growth: take it now
             g[a].members.insert(g[a].members.end(), g[b].members.begin(), g[b].members.end());
             g[b].alive = false;
@@ -78,7 +80,6 @@ qt_status fuse_circuit(const Circuit& c, uint32_t kmax, Fused& f) {
     const Op& op = c.ops[i];
     uint64_t m = 0;
     for (uint32_t b = 0; b < op.q; ++b) m |= 1ull << op.qubits[b];
-    if (op.q > kmax) return set_error(QT_ERR_UNSUPPORTED, "qt_fuse: op %u has %u qubits > fuse size %u", i, op.q, kmax);
     g.push_back(Work{m, {i}, true});
     if (op.kind == QT_OP_GATE) f.gate_ops++;
   }

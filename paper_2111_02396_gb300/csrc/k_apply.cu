@@ -2,24 +2,34 @@
 //
 // The state is 2^n interleaved (re, im) float pairs.  A k-qubit fused gate
 // splits it into 2^(n-k) gather sets of 2^k amplitudes (the set's base
-// index with every combination of the target bits).  One thread owns one
-// set -- or, when qubit 0 is not a target, the two neighbouring sets that
-// differ only in bit 0, so that each member is one 128-bit load of two
-// adjacent amplitudes.  Consecutive threads own consecutive bases, so every
-// warp-wide load or store covers whole 128-byte lines however high the
-// target qubits are; low target qubits spread a warp's accesses over a few
-// more lines that the same warp reads or writes in its other members, so
-// DRAM still sees every byte once.
+// index with every combination of the target bits); each set is one
+// 2^k x 2^k matrix-vector product.
+//
+// k_apply_tile (the main kernel): a CTA of 128 threads owns a tile of
+// 128 gather sets = 2^(7+k) amplitudes.  The tile is 2^h rows (h = number
+// of "high" targets) of 2^C contiguous amplitudes, where C is the smallest
+// width such that the row holds every "low" target plus 7 free bits; so a
+// row is at least 1 KB and every warp-wide 128-bit load or store of the
+// tile is fully coalesced whatever the target pattern.  The tile is staged
+// in shared memory with an XOR swizzle (8-byte slot ^= bits 4..7 of the
+// index) that keeps the strided gathers of low-target patterns free of bank
+// conflicts.  Each thread then gathers one set, multiplies, and scatters
+// it back; the tile is stored with the same coalesced pattern.
 //
 // The matrix is a __grid_constant__ kernel parameter: with the loops over
-// rows and columns fully unrolled every matrix element is a constant-bank
-// operand of the FMA that uses it, so the inner product costs 4 FFMA per
-// complex multiply-add and no load instructions.  Each output row is stored
-// as soon as it is complete (all inputs are already in registers).
+// rows and columns unrolled every matrix entry is a constant-bank operand
+// of the FMA that uses it.  The complex products use the three-multiply
+// form: with U = c + i d and v = a + i b, precomputing e = c + d and
+// f = d - c per entry and s = a + b per amplitude,
+//   Re(U v) = sum c s - sum b e,   Im(U v) = sum c s + sum a f,
+// i.e. 3 FFMA per complex multiply-add instead of 4.
+//
+// k_apply (direct, for states smaller than one tile): one thread per
+// gather set (or per pair of sets that differ in bit 0), members loaded
+// straight into registers.
 //
 // Bytes per launch: 16 * 2^n (every amplitude read once and written once).
-// FLOPs per launch: 2^(k+2) * 2^(n+1) (the paper's count); at k <= 4 the
-// FMA rate needed at full HBM bandwidth stays below the CUDA-core peak.
+// FLOPs per launch: 2^(k+2) * 2^(n+1) (the paper's count).
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -54,7 +64,7 @@ __global__ void __launch_bounds__(256) k_apply(float2* __restrict__ psi,
       float4 v[M];
 #pragma unroll
       for (int m = 0; m < M; ++m) v[m] = __ldcs(reinterpret_cast<const float4*>(psi + base + a.offs[m]));
-#pragma unroll
+#pragma unroll 2
       for (int j = 0; j < M; ++j) {
         float xr = 0.f, xi = 0.f, yr = 0.f, yi = 0.f;
 #pragma unroll
@@ -75,7 +85,7 @@ __global__ void __launch_bounds__(256) k_apply(float2* __restrict__ psi,
       float2 v[M];
 #pragma unroll
       for (int m = 0; m < M; ++m) v[m] = __ldcs(psi + base + a.offs[m]);
-#pragma unroll
+#pragma unroll 2
       for (int j = 0; j < M; ++j) {
         float xr = 0.f, xi = 0.f;
 #pragma unroll
@@ -103,6 +113,164 @@ int sm_count() {
   });
   return g_sms;
 }
+
+
+// ---------------------------------------------------------------------------
+// tiled kernel
+// ---------------------------------------------------------------------------
+constexpr int kTileThreads = 128;       // = gather sets per tile
+
+template <int K>
+struct TileArgs {
+  float c[1 << K][1 << K];    // Re U
+  float e[1 << K][1 << K];    // Re U + Im U
+  float f[1 << K][1 << K];    // Im U - Re U
+  uint64_t roff[1 << K];      // memory offset of tile row r
+  uint32_t moff[1 << K];      // tile-local offset of member m
+  uint32_t tins[K];           // tile-local target positions, ascending
+  uint32_t hins[K];           // memory positions of the high targets, ascending
+  int nh;                     // number of high targets
+  int C;                      // contiguous low bits per row
+  uint64_t num_tiles;
+};
+
+__device__ __forceinline__ uint32_t swz(uint32_t l) { return l ^ ((l >> 4) & 15u); }
+
+template <int K>
+__global__ void __launch_bounds__(kTileThreads) k_apply_tile(float2* __restrict__ psi,
+                                                             const __grid_constant__ TileArgs<K> a) {
+  constexpr int M = 1 << K;
+  constexpr int TILE = kTileThreads * M;       // amplitudes per tile
+  constexpr int CHUNKS = TILE / 2;             // float4 chunks per tile
+  __shared__ __align__(16) float2 sm[TILE];
+  const uint32_t tid = threadIdx.x;
+  const uint32_t rowmask = (1u << a.C) - 1u;
+  // this thread's gather set inside the tile (same for every tile)
+  uint32_t sbase = tid;
+#pragma unroll
+  for (int b = 0; b < K; ++b) {
+    const uint32_t t = a.tins[b];
+    sbase = ((sbase >> t) << (t + 1)) | (sbase & ((1u << t) - 1u));
+  }
+  for (uint64_t tile = blockIdx.x; tile < a.num_tiles; tile += gridDim.x) {
+    uint64_t base = tile << a.C;
+    for (int j = 0; j < a.nh; ++j) {
+      const uint32_t h = a.hins[j];
+      base = ((base >> h) << (h + 1)) | (base & ((1ull << h) - 1ull));
+    }
+    // load rows -> shared (coalesced 128-bit)
+    float4 buf[CHUNKS / kTileThreads];
+#pragma unroll
+    for (int i = 0; i < CHUNKS / kTileThreads; ++i) {
+      const uint32_t l = 2u * (tid + i * kTileThreads);
+      buf[i] = __ldcs(reinterpret_cast<const float4*>(psi + (base | a.roff[l >> a.C] | (l & rowmask))));
+    }
+#pragma unroll
+    for (int i = 0; i < CHUNKS / kTileThreads; ++i) {
+      const uint32_t l = 2u * (tid + i * kTileThreads);
+      const uint32_t fl = (l >> 4) & 15u;
+      float4 v = buf[i];
+      if (fl & 1u) v = make_float4(v.z, v.w, v.x, v.y);
+      *reinterpret_cast<float4*>(&sm[(l ^ fl) & ~1u]) = v;
+    }
+    __syncthreads();
+    // one gather set per thread
+    float va[M], vb[M], vs[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      const float2 v = sm[swz(sbase | a.moff[m])];
+      va[m] = v.x;
+      vb[m] = v.y;
+      vs[m] = v.x + v.y;
+    }
+    // rows two at a time: the matrix entries come in through uniform
+    // constant loads (warp-uniform row index); a full unroll would make the
+    // compiler keep far more values live and spill
+#pragma unroll 2
+    for (int j = 0; j < M; ++j) {
+      float t = 0.f, r = 0.f, im = 0.f;
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        t = fmaf(a.c[j][m], vs[m], t);
+        r = fmaf(a.e[j][m], vb[m], r);
+        im = fmaf(a.f[j][m], va[m], im);
+      }
+      sm[swz(sbase | a.moff[j])] = make_float2(t - r, t + im);
+    }
+    __syncthreads();
+    // shared -> rows (coalesced 128-bit)
+#pragma unroll
+    for (int i = 0; i < CHUNKS / kTileThreads; ++i) {
+      const uint32_t l = 2u * (tid + i * kTileThreads);
+      const uint32_t fl = (l >> 4) & 15u;
+      float4 v = *reinterpret_cast<const float4*>(&sm[(l ^ fl) & ~1u]);
+      if (fl & 1u) v = make_float4(v.z, v.w, v.x, v.y);
+      __stcs(reinterpret_cast<float4*>(psi + (base | a.roff[l >> a.C] | (l & rowmask))), v);
+    }
+    __syncthreads();
+  }
+}
+
+template <int K>
+static cudaError_t launch_tile(float2* psi, int n, const uint32_t* targets, const float2* U,
+                               cudaStream_t st) {
+  static int occ = 0;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_apply_tile<K>, kTileThreads, 0);
+    if (occ <= 0) occ = 1;
+  });
+  constexpr int M = 1 << K;
+  TileArgs<K> a;
+  for (int j = 0; j < M; ++j)
+    for (int m = 0; m < M; ++m) {
+      const float re = U[j * M + m].x, im = U[j * M + m].y;
+      a.c[j][m] = re;
+      a.e[j][m] = re + im;
+      a.f[j][m] = im - re;
+    }
+  // C = 7 + number of targets below C
+  int C = 7;
+  for (;;) {
+    int low = 0;
+    for (int b = 0; b < K; ++b) low += targets[b] < static_cast<uint32_t>(C);
+    if (C - low >= 7) break;
+    ++C;
+  }
+  a.C = C;
+  int nh = 0;
+  uint32_t tpos[K];
+  for (int b = 0; b < K; ++b) {
+    if (targets[b] < static_cast<uint32_t>(C)) {
+      tpos[b] = targets[b];
+    } else {
+      tpos[b] = static_cast<uint32_t>(C + nh);
+      a.hins[nh++] = targets[b];
+    }
+  }
+  a.nh = nh;
+  for (int b = 0; b < K; ++b) a.tins[b] = tpos[b];   // ascending: low targets, then C, C+1, ...
+  for (int m = 0; m < M; ++m) {
+    uint32_t o = 0;
+    for (int b = 0; b < K; ++b)
+      if ((m >> b) & 1) o |= 1u << tpos[b];
+    a.moff[m] = o;
+  }
+  for (int r = 0; r < M; ++r) {
+    uint64_t o = 0;
+    for (int j = 0; j < nh; ++j)
+      if ((r >> j) & 1) o |= 1ull << a.hins[j];
+    a.roff[r] = r < (1 << nh) ? o : 0;
+  }
+  a.num_tiles = 1ull << (n - C - nh);
+  const uint64_t cap = static_cast<uint64_t>(sm_count()) * occ;
+  const unsigned grid = static_cast<unsigned>(a.num_tiles < cap ? a.num_tiles : cap);
+  k_apply_tile<K><<<grid, kTileThreads, 0, st>>>(psi, a);
+  return cudaGetLastError();
+}
+
+// smallest n for which one tile fits: 7 free bits + k targets
+static inline bool tile_fits(int n, int k) { return n >= 7 + k; }
 
 template <int K, bool PAIR>
 static cudaError_t launch_k(float2* psi, int n, const uint32_t* targets, const float2* U,
@@ -137,6 +305,16 @@ static cudaError_t launch_k(float2* psi, int n, const uint32_t* targets, const f
 cudaError_t launch_apply(float2* psi, int n, int k, const uint32_t* targets, const float2* U,
                          cudaStream_t st) {
   // targets ascending; pair mode needs qubit 0 free and at least one spare bit
+  if (tile_fits(n, k)) {
+    switch (k) {
+      case 1: return launch_tile<1>(psi, n, targets, U, st);
+      case 2: return launch_tile<2>(psi, n, targets, U, st);
+      case 3: return launch_tile<3>(psi, n, targets, U, st);
+      case 4: return launch_tile<4>(psi, n, targets, U, st);
+      case 5: return launch_tile<5>(psi, n, targets, U, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   const bool pair = (targets[0] != 0) && (n >= k + 1);
   switch (k) {
     case 1: return pair ? launch_k<1, true>(psi, n, targets, U, st) : launch_k<1, false>(psi, n, targets, U, st);

@@ -41,6 +41,8 @@ def test_apply_every_pattern(qt, orc, n, k):
         pytest.skip("k > n")
     rng = np.random.default_rng([n, k])
     for qubits in patterns(n, k, rng):
+        if max(qubits) >= n:
+            continue
         U = qs.random_unitary(1 << k, rng)
         psi = random_state(n, k)
         d = to_device(psi)
