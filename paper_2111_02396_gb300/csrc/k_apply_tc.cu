@@ -1,0 +1,402 @@
+// Fused-gate application on the 5th-generation tensor cores (tcgen05) for
+// wide fused gates (k = 5, 6), in split-TF32 with FP32 accumulation.
+//
+// Alg. 1 over a batch of gather sets is a dense contraction: with the 2^k
+// amplitudes of a set interleaved as 2^(k+1) reals a, the output set is
+// W a, W the real embedding of U (entry (j, m) of U = c + i d becomes the
+// 2x2 block [[c, -d], [d, c]]).  A tile of 128 sets is the matrix
+// A [128 x K] (K = 2^(k+1)), and D = A B with B = W^T [K x N], N = K.
+// Sec. III.A counts 2^(q-1) flop per byte: 32 at q = 6, well above what
+// CUDA cores sustain at HBM speed, so the contraction goes to tcgen05.mma.
+//
+// Precision: each FP32 operand x is split into x_hi = tf32(x) and
+// x_lo = tf32(x - x_hi); D = A_hi B_hi + A_hi B_lo + A_lo B_hi accumulates
+// in FP32 (the three-pass split-TF32 scheme, Ootomo & Yokota 2022), which
+// leaves only the A_lo B_lo term (~2^-22 relative) out.
+//
+// Data flow (one persistent CTA per SM, 9 warps):
+//   warps 0-3  loaders: thread t owns set t of the tile (TMEM lane t); it
+//              loads its set member by member (a warp reads 32 consecutive
+//              set bases per member: coalesced), splits hi/lo, and writes
+//              A to TMEM with tcgen05.st (A operand taken from TMEM).
+//   warp 8     MMA issuer: one elected thread issues tcgen05.mma (M=128,
+//              N=2^(k+1), K=8 per instruction) with A in TMEM and B in
+//              shared memory, and commits to mbarriers.
+//   warps 4-7  epilogue: tcgen05.ld of the accumulator rows, coalesced
+//              stores of the output sets.
+// TMEM (512 columns): two A slots of 128 columns (hi at +0, lo at +64; one
+// chunk of up to 32 members) and two accumulators of N columns (at 256 and
+// 256 + N), so the loaders fill the
+// next chunk while the tensor core works and the epilogue drains one tile
+// while the next accumulates.
+//
+// B (hi and lo) is staged once per CTA in shared memory in the K-major
+// no-swizzle layout: core matrices of 8 rows x 16 bytes; adjacent core
+// matrices along K are LBO = 128 bytes apart, along N SBO = 128 * K/4 bytes.
+//
+// Every mbarrier wait is bounded: on timeout the kernel sets *err, waits
+// (bounded) for its own MMAs to drain, frees its TMEM and returns.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "kernels.h"
+
+namespace qt {
+
+namespace tc {
+
+constexpr int kThreads = 288;           // 9 warps
+constexpr int kTileSets = 128;          // M
+constexpr int kMaxChunkReals = 64;      // K per A slot (up to 32 members)
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kSpinLimit = 1u << 22;   // x ~0.5 us nanosleep -> ~2 s bound
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait; false on timeout (and *err is set)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
+  for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*reinterpret_cast<volatile int*>(err)) return false;
+    __nanosleep(256);
+  }
+  atomicOr(err, code);
+  return false;
+}
+
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// 32 consecutive 32-bit columns of this thread's lane
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+      "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
+      "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
+      "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// D[tmem] (+)= A[tmem] * B[smem desc]
+__device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// shared-memory matrix descriptor, K-major, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((addr >> 4) & 0x3FFFu);
+  d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16;
+  d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32;
+  d |= 1ull << 46;          // descriptor version for tcgen05
+  return d;                 // base offset 0, layout type 0 (no swizzle)
+}
+
+// instruction descriptor: D f32, A/B tf32, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+}  // namespace tc
+
+template <int K>
+struct TcArgs {
+  uint64_t moff[1 << K];     // memory offset of member m within a set
+  uint32_t ins[K];           // ascending target positions (insert zeros)
+  uint64_t num_tiles;        // tiles of 128 sets
+  const float* bmat;         // W row-major [N x N] FP32 (N = 2^(K+1)), device
+  int* err;                  // device error flag
+  uint32_t lbo, sbo;         // B descriptor offsets (bytes)
+};
+
+template <int K>
+__global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict__ psi, const __grid_constant__ TcArgs<K> a) {
+  using namespace tc;
+  constexpr int NM = 1 << K;                 // members per set
+  constexpr int N = 2 * NM;                  // reals per set = K dim = N dim
+  constexpr int CR = N < kMaxChunkReals ? N : kMaxChunkReals;   // reals per A chunk
+  constexpr int NCHUNK = N / CR;             // A chunks per tile (1 or 2)
+  constexpr int MPC = CR / 2;                // members per chunk (16 or 32)
+  constexpr uint32_t IDESC = idesc_tf32(kTileSets, N);
+  extern __shared__ __align__(1024) uint8_t smem[];
+  float* bhi = reinterpret_cast<float*>(smem);
+  float* blo = bhi + N * N;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(blo + N * N);
+  uint64_t* a_full = bars;         // [2]
+  uint64_t* a_empty = bars + 2;    // [2]
+  uint64_t* d_full = bars + 4;     // [2]
+  uint64_t* d_empty = bars + 6;    // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 8);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  // stage B = W^T (hi, lo) in the K-major core-matrix layout: element
+  // (n, k) of B^T-as-stored (row n of W, column k) at
+  // (n/8)*SBO + (k/4)*LBO + (n%8)*16 + (k%4)*4
+  for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
+    const int n = i / N, k = i % N;
+    const float w = a.bmat[i];
+    const float hi = __uint_as_float(to_tf32(w));
+    const float lo = __uint_as_float(to_tf32(w - hi));
+    const uint32_t off = (n >> 3) * a.sbo + (k >> 2) * a.lbo + (n & 7) * 16 + (k & 3) * 4;
+    *reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(bhi) + off) = hi;
+    *reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(blo) + off) = lo;
+  }
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&a_full[i], 128);
+      mbar_init(&a_empty[i], 1);
+      mbar_init(&d_full[i], 1);
+      mbar_init(&d_empty[i], 128);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // make the generic-proxy B stores visible to the tensor core (async proxy)
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (warp == 8) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  // column map: A slot s at s*128 (hi: +0, lo: +64); accumulator d at 256 + d*N
+  const uint32_t a_col0 = 0, d_col0 = 256;
+
+  if (warp < 4) {
+    // ---------------- loaders ----------------
+    const uint32_t lane_base = static_cast<uint32_t>(warp * 32) << 16;
+    uint32_t chunk_iter = 0;
+    for (uint64_t tile = blockIdx.x; tile < a.num_tiles; tile += gridDim.x) {
+      uint64_t base = tile * kTileSets + threadIdx.x;
+#pragma unroll
+      for (int b = 0; b < K; ++b) {
+        const uint32_t s = a.ins[b];
+        base = ((base >> s) << (s + 1)) | (base & ((1ull << s) - 1ull));
+      }
+      bool ok = true;
+      for (int c = 0; c < NCHUNK; ++c, ++chunk_iter) {
+        const uint32_t slot = chunk_iter & 1;
+        const uint32_t use = chunk_iter >> 1;
+        if (use > 0 && !mbar_wait(&a_empty[slot], (use - 1) & 1, a.err, 1)) { ok = false; break; }
+        uint32_t hi[32], lo[32];
+#pragma unroll
+        for (int half = 0; half < MPC / 16; ++half) {
+#pragma unroll
+          for (int m = 0; m < 16; ++m) {
+            const float2 v = __ldcs(psi + base + a.moff[c * MPC + half * 16 + m]);
+            const uint32_t hr = to_tf32(v.x), hm = to_tf32(v.y);
+            hi[2 * m] = hr;
+            hi[2 * m + 1] = hm;
+            lo[2 * m] = to_tf32(v.x - __uint_as_float(hr));
+            lo[2 * m + 1] = to_tf32(v.y - __uint_as_float(hm));
+          }
+          const uint32_t col = a_col0 + slot * 128 + half * 32;
+          tmem_st32(tmem + lane_base + col, hi);
+          tmem_st32(tmem + lane_base + col + 64, lo);
+        }
+        tmem_wait_st();
+        fence_before();
+        mbar_arrive(&a_full[slot]);
+      }
+      if (!ok) break;
+    }
+  } else if (warp < 8) {
+    // ---------------- epilogue ----------------
+    const int w4 = warp - 4;
+    const uint32_t lane_base = static_cast<uint32_t>(w4 * 32) << 16;
+    const uint32_t t_in_tile = static_cast<uint32_t>(w4 * 32 + lane);
+    uint32_t iter = 0;
+    for (uint64_t tile = blockIdx.x; tile < a.num_tiles; tile += gridDim.x, ++iter) {
+      const uint32_t db = iter & 1;
+      if (!mbar_wait(&d_full[db], (iter >> 1) & 1, a.err, 2)) break;
+      fence_after();
+      uint64_t base = tile * kTileSets + t_in_tile;
+#pragma unroll
+      for (int b = 0; b < K; ++b) {
+        const uint32_t s = a.ins[b];
+        base = ((base >> s) << (s + 1)) | (base & ((1ull << s) - 1ull));
+      }
+#pragma unroll
+      for (int cb = 0; cb < N / 32; ++cb) {
+        uint32_t v[32];
+        tmem_ld32(tmem + lane_base + d_col0 + db * N + cb * 32, v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          __stcs(psi + base + a.moff[cb * 16 + j], make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1])));
+      }
+      fence_before();
+      mbar_arrive(&d_empty[db]);
+    }
+  } else {
+    // ---------------- MMA issuer (warp 8) ----------------
+    uint32_t chunk_iter = 0, iter = 0;
+    const uint32_t bhi_addr = smem_u32(bhi), blo_addr = smem_u32(blo);
+    bool ok = true;
+    for (uint64_t tile = blockIdx.x; tile < a.num_tiles && ok; tile += gridDim.x, ++iter) {
+      const uint32_t db = iter & 1;
+      if (iter >= 2 && !mbar_wait(&d_empty[db], ((iter >> 1) - 1) & 1, a.err, 4)) { ok = false; break; }
+      const uint32_t d_tmem = tmem + d_col0 + db * N;
+      for (int c = 0; c < NCHUNK; ++c, ++chunk_iter) {
+        const uint32_t slot = chunk_iter & 1;
+        if (!mbar_wait(&a_full[slot], (chunk_iter >> 1) & 1, a.err, 8)) { ok = false; break; }
+        fence_after();
+        if (lane == 0) {
+#pragma unroll
+          for (int kk = 0; kk < CR / 8; ++kk) {
+            const int kglob = c * CR + kk * 8;                           // K offset in B
+            const uint32_t a_hi = tmem + a_col0 + slot * 128 + kk * 8;
+            const uint32_t a_lo = a_hi + 64;
+            const uint64_t dhi = smem_desc(bhi_addr + (kglob >> 2) * a.lbo, a.lbo, a.sbo);
+            const uint64_t dlo = smem_desc(blo_addr + (kglob >> 2) * a.lbo, a.lbo, a.sbo);
+            mma_ts(d_tmem, a_hi, dhi, IDESC, (c > 0 || kk > 0) ? 1u : 0u);
+            mma_ts(d_tmem, a_hi, dlo, IDESC, 1u);
+            mma_ts(d_tmem, a_lo, dhi, IDESC, 1u);
+          }
+          mma_commit(&a_empty[slot]);
+        }
+        __syncwarp();
+      }
+      if (!ok) break;
+      if (lane == 0) mma_commit(&d_full[db]);
+      __syncwarp();
+    }
+  }
+  // teardown: the last commits cover all issued MMAs; the epilogue consumed
+  // every accumulator it waited for.  Wait for in-flight MMAs via a final
+  // commit on a private barrier before freeing TMEM.
+  __syncthreads();
+  if (warp == 8) {
+    __shared__ uint64_t drain;
+    if (lane == 0) {
+      mbar_init(&drain, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      mma_commit(&drain);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_wait(&drain, 0, a.err, 16);
+    __syncwarp();
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+template <int K>
+static cudaError_t launch_tc_k(float2* psi, int n, const uint32_t* targets, const float* wdev, int* err,
+                               cudaStream_t st, uint32_t lbo_override, uint32_t sbo_override) {
+  constexpr int N = 2 << K;
+  const size_t smem = 2 * sizeof(float) * N * N + 8 * sizeof(uint64_t) + 16;
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [&] {
+    attr_err = cudaFuncSetAttribute(k_apply_tc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  TcArgs<K> a;
+  for (int m = 0; m < (1 << K); ++m) {
+    uint64_t o = 0;
+    for (int b = 0; b < K; ++b)
+      if ((m >> b) & 1) o |= 1ull << targets[b];
+    a.moff[m] = o;
+  }
+  for (int b = 0; b < K; ++b) a.ins[b] = targets[b];
+  a.num_tiles = (1ull << (n - K)) / tc::kTileSets;
+  a.bmat = wdev;
+  a.err = err;
+  a.lbo = lbo_override ? lbo_override : 128;
+  a.sbo = sbo_override ? sbo_override : 128 * (N / 4);
+  uint64_t grid = static_cast<uint64_t>(sm_count());
+  if (grid > a.num_tiles) grid = a.num_tiles;
+  k_apply_tc<K><<<static_cast<unsigned>(grid), tc::kThreads, smem, st>>>(psi, a);
+  return cudaGetLastError();
+}
+
+bool tc_supported(int n, int k) { return k >= 4 && k <= 6 && n >= k + 7; }
+
+cudaError_t launch_apply_tc(float2* psi, int n, int k, const uint32_t* targets, const float* wdev, int* err,
+                            cudaStream_t st, uint32_t lbo, uint32_t sbo) {
+  if (!tc_supported(n, k)) return cudaErrorInvalidValue;
+  if (k == 4) return launch_tc_k<4>(psi, n, targets, wdev, err, st, lbo, sbo);
+  if (k == 5) return launch_tc_k<5>(psi, n, targets, wdev, err, st, lbo, sbo);
+  return launch_tc_k<6>(psi, n, targets, wdev, err, st, lbo, sbo);
+}
+
+void real_embedding(int k, const float2* U, float* W) {
+  const int NM = 1 << k, N = 2 * NM;
+  for (int j = 0; j < NM; ++j)
+    for (int m = 0; m < NM; ++m) {
+      const float c = U[j * NM + m].x, d = U[j * NM + m].y;
+      W[(2 * j) * N + 2 * m] = c;
+      W[(2 * j) * N + 2 * m + 1] = -d;
+      W[(2 * j + 1) * N + 2 * m] = d;
+      W[(2 * j + 1) * N + 2 * m + 1] = c;
+    }
+}
+
+}  // namespace qt

@@ -40,6 +40,13 @@ cudaError_t launch_expect(const float2* psi, int n, int nm, const uint64_t* mask
 // S samples of trajectory traj into out (device)
 cudaError_t launch_sample(const float2* psi, int n, uint64_t seed, uint64_t traj, uint32_t S,
                           uint64_t* out, const Scratch& scr, cudaStream_t st);
+// tensor-core path (split-TF32, k = 4..6, n >= k + 7): W is the real
+// embedding of U, row-major [2^(k+1) x 2^(k+1)] FP32 in device memory; *err
+// is set (nonzero) if a bounded wait in the kernel ran out
+bool tc_supported(int n, int k);
+cudaError_t launch_apply_tc(float2* psi, int n, int k, const uint32_t* targets, const float* wdev, int* err,
+                            cudaStream_t st, uint32_t lbo = 0, uint32_t sbo = 0);
+void real_embedding(int k, const float2* U, float* W);
 // |0...0>
 cudaError_t launch_init_state(float2* psi, int n, cudaStream_t st);
 // psi *= f

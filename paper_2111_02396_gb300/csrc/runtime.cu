@@ -181,6 +181,50 @@ struct Controller {
     for (auto e : ev) cudaEventDestroy(e);
   }
 
+  // tensor-core path buffers (split-TF32, widths 4..6)
+  DevBuf wbuf, errbuf;
+  std::vector<float> wtmp;
+
+  bool use_tc(int k) const {
+    return R.p.precision == QT_TF32X3 && tc_supported(static_cast<int>(R.n), k);
+  }
+
+  qt_status launch_one(float2* psi, const std::vector<uint32_t>& targets, const float2* U) {
+    const int k = static_cast<int>(targets.size());
+    if (use_tc(k)) {
+      if (!wbuf.p && (!wbuf.alloc(sizeof(float) * 128 * 128, R.st) || !errbuf.alloc(sizeof(int), R.st)))
+        return set_error(QT_ERR_OUT_OF_MEMORY, "tensor-core matrix buffer");
+      if (!err_cleared) {
+        QT_CUDA(cudaMemsetAsync(errbuf.p, 0, sizeof(int), R.st), "cudaMemsetAsync");
+        err_cleared = true;
+      }
+      const int N = 2 << k;
+      wtmp.resize(static_cast<size_t>(N) * N);
+      real_embedding(k, U, wtmp.data());
+      QT_CUDA(cudaMemcpyAsync(wbuf.p, wtmp.data(), sizeof(float) * N * N, cudaMemcpyHostToDevice, R.st),
+              "cudaMemcpyAsync(W)");
+      R.stats.h2d_bytes += sizeof(float) * N * N;
+      QT_CUDA(launch_apply_tc(psi, static_cast<int>(R.n), k, targets.data(), wbuf.as<float>(), errbuf.as<int>(), R.st),
+              "tensor-core apply kernel launch");
+      return QT_OK;
+    }
+    if (k > 5) return set_error(QT_ERR_UNSUPPORTED, "fused width %d needs precision QT_TF32X3 (n >= %d)", k, k + 7);
+    QT_CUDA(launch_apply(psi, static_cast<int>(R.n), k, targets.data(), U, R.st), "apply kernel launch");
+    const size_t d = 1ull << k;
+    R.stats.h2d_bytes += sizeof(float2) * d * d;
+    return QT_OK;
+  }
+  bool err_cleared = false;
+
+  qt_status check_device_error() {
+    if (!errbuf.p) return QT_OK;
+    int e = 0;
+    QT_CUDA(cudaMemcpyAsync(&e, errbuf.p, sizeof(int), cudaMemcpyDeviceToHost, R.st), "cudaMemcpyAsync(err)");
+    QT_CUDA(cudaStreamSynchronize(R.st), "cudaStreamSynchronize(err)");
+    if (e) return set_error(QT_ERR_TIMEOUT, "tensor-core kernel: a bounded wait ran out (code %d)", e);
+    return QT_OK;
+  }
+
   qt_status apply(float2* psi, const std::vector<uint32_t>& targets, const float2* U) {
     const bool timed = (R.p.flags & QT_FLAG_TIME_KERNELS) != 0;
     if (timed) {
@@ -193,8 +237,8 @@ struct Controller {
       }
       QT_CUDA(cudaEventRecord(ev[ev_used], R.st), "cudaEventRecord");
     }
-    QT_CUDA(launch_apply(psi, static_cast<int>(R.n), static_cast<int>(targets.size()), targets.data(), U, R.st),
-            "apply kernel launch");
+    qt_status ls = launch_one(psi, targets, U);
+    if (ls != QT_OK) return ls;
     if (timed) {
       QT_CUDA(cudaEventRecord(ev[ev_used + 1], R.st), "cudaEventRecord");
       ev_used += 2;
@@ -202,8 +246,6 @@ struct Controller {
     R.stats.fused_passes++;
     R.stats.kernel_launches++;
     R.stats.apply_bytes += 16ull << R.n;
-    const size_t d = 1ull << targets.size();
-    R.stats.h2d_bytes += sizeof(float2) * d * d;
     return QT_OK;
   }
 
@@ -411,8 +453,9 @@ qt_status qt_run_trajectories(const qt_fused* f, const qt_run_params* p, qt_run*
   const Circuit& c = *f->c;
   if (c.n < 1) return set_error(QT_ERR_INVALID_ARG, "qt_run_trajectories: empty circuit");
   for (const auto& g : f->gates)
-    if (g.targets.size() > 5)
-      return set_error(QT_ERR_UNSUPPORTED, "qt_run_trajectories: fused width %zu > 5 not built", g.targets.size());
+    if (g.targets.size() > 5 && !(p->precision == QT_TF32X3 && tc_supported(static_cast<int>(c.n), 6)))
+      return set_error(QT_ERR_UNSUPPORTED,
+                       "qt_run_trajectories: fused width %zu needs precision QT_TF32X3 and n >= 13", g.targets.size());
   std::unique_ptr<qt_run> R(new (std::nothrow) qt_run());
   if (!R) return set_error(QT_ERR_OUT_OF_MEMORY, "qt_run_trajectories: host allocation");
   R->f = f;
@@ -459,6 +502,8 @@ qt_status qt_run_trajectories(const qt_fused* f, const qt_run_params* p, qt_run*
     s = ctl.measure(t, psi, dsamp.as<uint64_t>());
     if (s != QT_OK) return s;
     s = ctl.collect_timing();
+    if (s != QT_OK) return s;
+    s = ctl.check_device_error();
     if (s != QT_OK) return s;
   }
   QT_CUDA(cudaEventRecord(e1, R->st), "cudaEventRecord");
@@ -589,7 +634,9 @@ qt_status qt_state_apply(void* state, uint32_t n, uint32_t q, const uint32_t* qu
   clear_error();
   qt_status s = check_state(state, n, "qt_state_apply");
   if (s != QT_OK) return s;
-  if (q < 1 || q > n || q > 5) return set_error(QT_ERR_UNSUPPORTED, "qt_state_apply: q=%u (1..min(n,5))", q);
+  const bool tc = precision == QT_TF32X3 && tc_supported(static_cast<int>(n), static_cast<int>(q));
+  if (q < 1 || q > n || q > 6 || (q == 6 && !tc))
+    return set_error(QT_ERR_UNSUPPORTED, "qt_state_apply: q=%u (1..min(n,5); 6 with QT_TF32X3 and n >= 13)", q);
   if (precision != QT_FP32 && precision != QT_TF32X3) return set_error(QT_ERR_INVALID_ARG, "qt_state_apply: precision");
   if (!U) return set_error(QT_ERR_INVALID_ARG, "qt_state_apply: U is NULL");
   s = check_qubits(n, q, qubits, "qt_state_apply");
@@ -613,8 +660,26 @@ qt_status qt_state_apply(void* state, uint32_t n, uint32_t q, const uint32_t* qu
       const size_t e = static_cast<size_t>(perm(i)) * D + perm(j);
       M[static_cast<size_t>(i) * D + j] = make_float2(static_cast<float>(U[2 * e]), static_cast<float>(U[2 * e + 1]));
     }
-  QT_CUDA(launch_apply(static_cast<float2*>(state), static_cast<int>(n), static_cast<int>(q), sorted.data(), M.data(),
-                       static_cast<cudaStream_t>(stream)),
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (tc) {
+    const int N = 2 << q;
+    std::vector<float> W(static_cast<size_t>(N) * N);
+    real_embedding(static_cast<int>(q), M.data(), W.data());
+    DevBuf wd, ed;
+    if (!wd.alloc(sizeof(float) * N * N, st) || !ed.alloc(sizeof(int), st))
+      return set_error(QT_ERR_OUT_OF_MEMORY, "qt_state_apply: matrix buffer");
+    QT_CUDA(cudaMemsetAsync(ed.p, 0, sizeof(int), st), "cudaMemsetAsync");
+    QT_CUDA(cudaMemcpyAsync(wd.p, W.data(), sizeof(float) * N * N, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
+    QT_CUDA(launch_apply_tc(static_cast<float2*>(state), static_cast<int>(n), static_cast<int>(q), sorted.data(),
+                            wd.as<float>(), ed.as<int>(), st),
+            "qt_state_apply (tensor cores)");
+    int e = 0;
+    QT_CUDA(cudaMemcpyAsync(&e, ed.p, sizeof(int), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+    QT_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    if (e) return set_error(QT_ERR_TIMEOUT, "qt_state_apply: tensor-core kernel wait ran out (code %d)", e);
+    return QT_OK;
+  }
+  QT_CUDA(launch_apply(static_cast<float2*>(state), static_cast<int>(n), static_cast<int>(q), sorted.data(), M.data(), st),
           "qt_state_apply");
   return QT_OK;
 }

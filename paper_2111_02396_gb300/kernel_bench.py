@@ -39,6 +39,7 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--reads", action="store_true", help="also time the read passes")
+    ap.add_argument("--tf32", action="store_true", help="split-TF32 tensor-core path (k = 4..6)")
     args = ap.parse_args(argv)
     pkg.load()
     n = args.n
@@ -65,9 +66,11 @@ def main(argv=None):
         q, _ = np.linalg.qr(rng.normal(size=(1 << k, 1 << k)) + 1j * rng.normal(size=(1 << k, 1 << k)))
         for pat in args.patterns:
             qubits = PATTERNS[pat](n, k)
-            ms, gbs = timeit(lambda: pkg.qt_state_apply(d.data_ptr(), n, qubits, q,
+            prec = pkg.QT_TF32X3 if args.tf32 else pkg.QT_FP32
+            ms, gbs = timeit(lambda: pkg.qt_state_apply(d.data_ptr(), n, qubits, q, precision=prec,
                                                         stream=st.cuda_stream), 16 << n)
-            rows.append(dict(kernel="apply", n=n, k=k, pattern=pat, qubits=qubits, ms=ms, gbs=gbs))
+            rows.append(dict(kernel="apply_tf32x3" if args.tf32 else "apply", n=n, k=k, pattern=pat,
+                             qubits=qubits, ms=ms, gbs=gbs))
             print(json.dumps(rows[-1]), flush=True)
     if args.reads:
         for q in (1, 2):

@@ -31,7 +31,8 @@ def patterns(n, k, rng):
     yield [0] + list(range(n - k + 1, n))                 # qubit 0 + high
     yield list(range(1, k + 1))                           # low, qubit 0 free
     yield [int(x) for x in rng.choice(n, k, replace=False)]   # random, unsorted
-    yield [int(x) for x in rng.choice(np.arange(1, n), k, replace=False)]
+    if n - 1 >= k:
+        yield [int(x) for x in rng.choice(np.arange(1, n), k, replace=False)]
 
 
 @pytest.mark.parametrize("n", [5, 11, 17])
@@ -50,6 +51,29 @@ def test_apply_every_pattern(qt, orc, n, k):
         got = d.cpu().numpy()
         want = orc.apply(psi.astype(np.complex128), qubits, U)
         assert rel_l2(got, want) < KERNEL_L2, (qubits, rel_l2(got, want))
+
+
+# split-TF32 on tensor cores: three TF32 products per term, so each product
+# carries ~3 * 2^-21 relative error and an output row sums 2^(k+1) of them;
+# 1e-5 relative L2 bounds one call
+TC_L2 = 1e-5
+
+
+@pytest.mark.parametrize("n", [13, 16, 19])
+@pytest.mark.parametrize("k", [4, 5, 6])
+def test_apply_tf32x3_every_pattern(qt, orc, n, k):
+    if n < k + 7:
+        pytest.skip("tensor-core path needs n >= k + 7")
+    rng = np.random.default_rng([n, k, 7])
+    for qubits in patterns(n, k, rng):
+        if max(qubits) >= n:
+            continue
+        U = qs.random_unitary(1 << k, rng)
+        psi = random_state(n, k)
+        d = to_device(psi)
+        qt.qt_state_apply(d.data_ptr(), n, qubits, U, precision=qt.QT_TF32X3)
+        want = orc.apply(psi.astype(np.complex128), qubits, U)
+        assert rel_l2(d.cpu().numpy(), want) < TC_L2, (qubits, rel_l2(d.cpu().numpy(), want))
 
 
 def test_apply_sequence_ragged_sizes(qt, orc):

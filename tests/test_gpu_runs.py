@@ -28,11 +28,12 @@ def qt():
     return pkg
 
 
-def compare_run(qt, orc, circ, T, *, k, mode, seed=0, S=0, masks=(), check_states=True):
+def compare_run(qt, orc, circ, T, *, k, mode, seed=0, S=0, masks=(), check_states=True,
+                precision=0):
     qc = qt.Circuit.from_synth(circ)
     f = qt.Fused(qc, k)
     run = qt.Run(f, T, seed=seed, mode=mode, samples_per_traj=S, z_masks=masks,
-                 keep_states=check_states)
+                 keep_states=check_states, precision=precision)
     kr, st = run.kraus_indices()
     omode = orc.DELAYED if mode == qt.QT_DELAYED else orc.EAGER
     ref = orc.run_trajectories(circ, T, mode=omode, seed=seed, keep_states=True)
@@ -95,6 +96,16 @@ def test_grid20_forced_flushes(qt, orc):
                            masks=[1 << j for j in range(20)])
     assert run.stats()["flushes"] > 0
     assert run.stats()["flushes"] == int(np.sum(ref["stage"] == 2))
+
+
+@pytest.mark.parametrize("k", [5, 6])
+def test_grid_depolarizing_tf32x3(qt, orc, k):
+    """Depolarizing-only grid circuit (the precision workload's generator at
+    n = 14) fused to k = 5, 6 and applied on tensor cores in split-TF32."""
+    circ = qs.config3_circuit(rows=2, cols=7, depth=12, p=0.02)
+    run, _ = compare_run(qt, orc, circ, 6, k=k, mode=qt.QT_DELAYED, S=100,
+                         precision=qt.QT_TF32X3)
+    assert run.stats()["flushes"] == 0
 
 
 def test_mixture_only_circuit_never_flushes(qt, orc):
