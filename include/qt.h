@@ -215,6 +215,24 @@ qt_status qt_state_sample(const void* state, uint32_t n, uint64_t seed, uint64_t
 qt_status qt_state_expect_z(const void* state, uint32_t n, uint32_t num_terms,
                             const uint64_t* z_masks, double* out, void* stream);
 
+/* Allocation-free variant of qt_state_reduced_density (no counterpart in the
+ * paper: it exists for callers that cannot let a library allocate device
+ * memory -- e.g. an application that reserves all GPU memory for its own pool
+ * at start-up, or a latency-critical loop that must not stall on cudaMalloc /
+ * cudaFree).  Same arguments, result and precision as
+ * qt_state_reduced_density; it calls no allocator of any kind.  Its FP64
+ * scratch is one fixed array inside libqt.so: 1216 * 64 + 64 doubles
+ * (608.5 KiB), which every GPU that loads the library holds until the process
+ * exits; q must be <= 3 (larger requests are rejected with
+ * QT_ERR_UNSUPPORTED and a message naming the limit).  The first call on a
+ * device looks up that array's device address with the device current; make
+ * that first call before any stream capture.  All calls share the array and
+ * it keeps the last call's contents (nothing in it needs to start at zero),
+ * so calls whose kernels overlap on the GPU -- different streams or host
+ * threads -- race: order them. */
+qt_status qt_state_reduced_density_noalloc(const void* state, uint32_t n, uint32_t q,
+                                           const uint32_t* qubits, double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

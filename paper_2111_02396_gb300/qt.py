@@ -72,6 +72,7 @@ EXPORTS = [
     "qt_circuit_destroy", "qt_fused_destroy", "qt_run_destroy", "qt_last_error",
     "qt_fused_info", "qt_fused_gate", "qt_channel_lower_bounds",
     "qt_state_apply", "qt_state_reduced_density", "qt_state_sample", "qt_state_expect_z",
+    "qt_state_reduced_density_noalloc",
 ]
 
 _lib = None
