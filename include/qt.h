@@ -215,6 +215,59 @@ qt_status qt_state_sample(const void* state, uint32_t n, uint64_t seed, uint64_t
 qt_status qt_state_expect_z(const void* state, uint32_t n, uint32_t num_terms,
                             const uint64_t* z_masks, double* out, void* stream);
 
+/* ---------------------------------------------------------------------- */
+/* Batched form: many small trajectories in one persistent launch          */
+/* ---------------------------------------------------------------------- */
+typedef struct qt_batch qt_batch;
+
+/* Gate fusion (Sec. III.B) of many circuits on host threads (0 = one per
+ * core); out[i] receives the fused handle of circuits[i]. */
+qt_status qt_fuse_many(uint32_t num, const qt_circuit* const* circuits, uint32_t max_fused_qubits,
+                       uint32_t threads, qt_fused** out);
+
+/* Pack num fused circuits (1..20 qubits, ops on <= 2 qubits, fused width
+ * <= 4) into device tables for the batched kernel; trajectory i of the batch
+ * runs fused[i].  Distinct operator sets are stored once.  The fused handles
+ * may be destroyed afterwards.  Errors: QT_ERR_INVALID_ARG,
+ * QT_ERR_UNSUPPORTED, QT_ERR_OUT_OF_MEMORY, QT_ERR_CUDA. */
+qt_status qt_batch_create(uint32_t num, const qt_fused* const* fused, qt_batch** out);
+
+typedef struct {
+  uint64_t seed;               /* Philox key */
+  uint64_t first_traj;         /* trajectory i of the batch uses id first_traj + i */
+  uint32_t samples_per_traj;   /* bitstrings per final state */
+  uint32_t keep_states;        /* 1: keep final states for qt_batch_state */
+  uint32_t use_graph;          /* replay the launch sequence as a CUDA graph (needs a stream) */
+  uint32_t threads;            /* CTA size: 128, 256 or 512 (0 = 512) */
+  void* stream;                /* cudaStream_t */
+} qt_batch_params;
+
+/* Run one trajectory of every circuit of the batch (Alg. 2, the same draws
+ * and decisions as qt_run_trajectories with the same seed and trajectory id)
+ * in one persistent kernel; blocks until the results are on the host. */
+qt_status qt_batch_run(qt_batch* b, const qt_batch_params* p);
+/* Samples of the last run: out[i * S + j], cap entries available. */
+qt_status qt_batch_samples(const qt_batch* b, uint64_t* out, size_t cap);
+/* Branch records of trajectory i of the last run (as qt_run_kraus_indices). */
+qt_status qt_batch_kraus_indices(const qt_batch* b, uint32_t i, int32_t* kraus, int32_t* stage, size_t cap,
+                                 uint32_t* num_channels);
+/* Normalized final state of trajectory i (needs keep_states), complex64 on the host. */
+qt_status qt_batch_state(const qt_batch* b, uint32_t i, void* dst, size_t bytes);
+typedef struct {
+  uint32_t num_traj, num_channels;
+  uint64_t total_amps, fused_gates, gate_ops, flushes;
+  double device_ms;            /* device time of the last run (events) */
+} qt_batch_stats_t;
+qt_status qt_batch_stats(const qt_batch* b, qt_batch_stats_t* out);
+void qt_batch_destroy(qt_batch* b);
+/* Autotuner of the batched form: on a spread sample of `sample` circuits
+ * (0 = 256) it fuses at every width kmin..kmax (<= 4), times the batched
+ * kernel (warm-up + 2 timed runs) at 128, 256 and 512 threads per CTA, and
+ * returns the fastest width and CTA size.  table (optional) receives the
+ * mean ms per run, [(k - kmin) * 3 + {128, 256, 512}]. */
+qt_status qt_batch_autotune(uint32_t num, const qt_circuit* const* circuits, uint32_t sample, uint32_t kmin,
+                            uint32_t kmax, void* stream, uint32_t* best_k, uint32_t* best_threads, double* table);
+
 /* Allocation-free variant of qt_state_reduced_density (no counterpart in the
  * paper: it exists for callers that cannot let a library allocate device
  * memory -- e.g. an application that reserves all GPU memory for its own pool

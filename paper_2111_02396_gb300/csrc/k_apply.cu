@@ -5,7 +5,7 @@
 // index with every combination of the target bits); each set is one
 // 2^k x 2^k matrix-vector product.
 //
-// k_apply_tile (the main kernel): a CTA of 128 threads owns a tile of
+// k_apply_tile (the main kernel): a CTA of 128 threads owns one tile of
 // 128 gather sets = 2^(7+k) amplitudes.  The tile is 2^h rows (h = number
 // of "high" targets) of 2^C contiguous amplitudes, where C is the smallest
 // width such that the row holds every "low" target plus 7 free bits; so a
@@ -152,7 +152,10 @@ __global__ void __launch_bounds__(kTileThreads) k_apply_tile(float2* __restrict_
     const uint32_t t = a.tins[b];
     sbase = ((sbase >> t) << (t + 1)) | (sbase & ((1u << t) - 1u));
   }
-  for (uint64_t tile = blockIdx.x; tile < a.num_tiles; tile += gridDim.x) {
+  // one tile per CTA: a loop over tiles would make the matrix entries
+  // loop-invariant, and the compiler would then hold them in registers
+  {
+    const uint64_t tile = blockIdx.x;
     uint64_t base = tile << a.C;
     for (int j = 0; j < a.nh; ++j) {
       const uint32_t h = a.hins[j];
@@ -214,12 +217,6 @@ __global__ void __launch_bounds__(kTileThreads) k_apply_tile(float2* __restrict_
 template <int K>
 static cudaError_t launch_tile(float2* psi, int n, const uint32_t* targets, const float2* U,
                                cudaStream_t st) {
-  static int occ = 0;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_apply_tile<K>, kTileThreads, 0);
-    if (occ <= 0) occ = 1;
-  });
   constexpr int M = 1 << K;
   TileArgs<K> a;
   for (int j = 0; j < M; ++j)
@@ -263,9 +260,7 @@ static cudaError_t launch_tile(float2* psi, int n, const uint32_t* targets, cons
     a.roff[r] = r < (1 << nh) ? o : 0;
   }
   a.num_tiles = 1ull << (n - C - nh);
-  const uint64_t cap = static_cast<uint64_t>(sm_count()) * occ;
-  const unsigned grid = static_cast<unsigned>(a.num_tiles < cap ? a.num_tiles : cap);
-  k_apply_tile<K><<<grid, kTileThreads, 0, st>>>(psi, a);
+  k_apply_tile<K><<<static_cast<unsigned>(a.num_tiles), kTileThreads, 0, st>>>(psi, a);
   return cudaGetLastError();
 }
 

@@ -185,8 +185,10 @@ struct Controller {
   DevBuf wbuf, errbuf;
   std::vector<float> wtmp;
 
+  // QT_TF32X3 sends 5- and 6-qubit pieces to the tensor cores; narrower
+  // pieces stay on the CUDA-core kernel, which is faster for them
   bool use_tc(int k) const {
-    return R.p.precision == QT_TF32X3 && tc_supported(static_cast<int>(R.n), k);
+    return R.p.precision == QT_TF32X3 && k >= 5 && tc_supported(static_cast<int>(R.n), k);
   }
 
   qt_status launch_one(float2* psi, const std::vector<uint32_t>& targets, const float2* U) {

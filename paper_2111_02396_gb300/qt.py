@@ -62,6 +62,24 @@ class qt_fused_info_t(C.Structure):
                 ("num_ops", C.c_uint32), ("num_channels", C.c_uint32)]
 
 
+class qt_batch_params(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("first_traj", C.c_uint64), ("samples_per_traj", C.c_uint32),
+                ("keep_states", C.c_uint32), ("use_graph", C.c_uint32), ("threads", C.c_uint32),
+                ("stream", C.c_void_p)]
+
+
+class qt_batch_stats_t(C.Structure):
+    _fields_ = [("num_traj", C.c_uint32), ("num_channels", C.c_uint32), ("total_amps", C.c_uint64),
+                ("fused_gates", C.c_uint64), ("gate_ops", C.c_uint64), ("flushes", C.c_uint64),
+                ("device_ms", C.c_double)]
+
+
+# qt_op as a numpy record (56 bytes, C layout) for vectorized marshalling
+QT_OP_DTYPE = np.dtype({"names": ["kind", "moment", "num_qubits", "qubits", "num_ops", "probs", "mats"],
+                        "formats": ["<i4", "<u4", "<u4", ("<u4", 6), "<u4", "<u8", "<u8"],
+                        "offsets": [0, 4, 8, 12, 36, 40, 48], "itemsize": 56})
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
@@ -73,6 +91,8 @@ EXPORTS = [
     "qt_fused_info", "qt_fused_gate", "qt_channel_lower_bounds",
     "qt_state_apply", "qt_state_reduced_density", "qt_state_sample", "qt_state_expect_z",
     "qt_state_reduced_density_noalloc",
+    "qt_fuse_many", "qt_batch_create", "qt_batch_run", "qt_batch_samples", "qt_batch_kraus_indices",
+    "qt_batch_state", "qt_batch_stats", "qt_batch_destroy", "qt_batch_autotune",
 ]
 
 _lib = None
@@ -113,12 +133,21 @@ def load(build_if_missing: bool = True):
             "qt_state_reduced_density": [P, u32, u32, P, P, P],
             "qt_state_sample": [P, u32, u64, u64, u32, P, P],
             "qt_state_expect_z": [P, u32, u32, P, P, P],
+            "qt_state_reduced_density_noalloc": [P, u32, u32, P, P, P],
+            "qt_fuse_many": [u32, P, u32, u32, P],
+            "qt_batch_create": [u32, P, P],
+            "qt_batch_run": [P, P],
+            "qt_batch_samples": [P, P, C.c_size_t],
+            "qt_batch_kraus_indices": [P, u32, P, P, C.c_size_t, P],
+            "qt_batch_state": [P, u32, P, C.c_size_t],
+            "qt_batch_stats": [P, P],
+            "qt_batch_autotune": [u32, P, u32, u32, u32, P, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
             fn.argtypes = args
             fn.restype = C.c_int
-        for name in ("qt_circuit_destroy", "qt_fused_destroy", "qt_run_destroy"):
+        for name in ("qt_circuit_destroy", "qt_fused_destroy", "qt_run_destroy", "qt_batch_destroy"):
             fn = getattr(lib, name)
             fn.argtypes = [P]
             fn.restype = None
@@ -207,7 +236,44 @@ class Circuit:
 
     @classmethod
     def from_synth(cls, circ):
+        if hasattr(circ, "table_id"):
+            return cls.from_compact(circ)
         return cls(circ.num_qubits, circ.ops)
+
+    @classmethod
+    def from_compact(cls, cc):
+        """From a qtsynth.CompactCircuit: the qt_op array is built in one
+        vectorized pass, every op pointing at its shared operator table entry."""
+        lib = load()
+        self = cls.__new__(cls)
+        self.num_qubits = int(cc.num_qubits)
+        mats_tab, probs_tab = [], []
+        mptr = np.zeros(len(cc.table), np.uint64)
+        pptr = np.zeros(len(cc.table), np.uint64)
+        nops = np.zeros(len(cc.table), np.uint32)
+        for t, (kind, mats, probs) in enumerate(cc.table):
+            m = np.ascontiguousarray(np.asarray(mats, np.complex128)).view(np.float64).ravel()
+            mats_tab.append(m)
+            mptr[t] = m.ctypes.data
+            nops[t] = np.asarray(mats).shape[0]
+            if probs is not None:
+                pr = np.ascontiguousarray(probs, np.float64)
+                probs_tab.append(pr)
+                pptr[t] = pr.ctypes.data
+        arr = np.zeros(cc.num_ops, QT_OP_DTYPE)
+        arr["kind"] = cc.kind
+        arr["moment"] = cc.moment
+        arr["num_qubits"] = cc.nq
+        arr["qubits"][:, :2] = cc.qubits
+        arr["num_ops"] = nops[cc.table_id]
+        arr["probs"] = pptr[cc.table_id]
+        arr["mats"] = mptr[cc.table_id]
+        self.h = C.c_void_p()
+        _check(lib.qt_circuit_create(self.num_qubits, cc.num_ops, arr.ctypes.data, C.byref(self.h)))
+        self.num_channels = cc.num_channels
+        self.num_ops = cc.num_ops
+        self._keep = None
+        return self
 
     def lower_bounds(self, channel):
         lib = load()
@@ -340,3 +406,95 @@ def qt_state_expect_z(state_ptr, n, masks, stream=None):
     out = np.zeros(max(len(m), 1))
     _check(load().qt_state_expect_z(state_ptr, n, len(m), _ptr(m), _ptr(out), stream))
     return out[:len(m)]
+
+
+# ----------------------------------------------------------------------------
+# batched form
+# ----------------------------------------------------------------------------
+def fuse_many(circuits, max_fused_qubits=0, threads=0):
+    """qt_fuse_many: fuse every circuit on host threads; returns Fused handles."""
+    lib = load()
+    n = len(circuits)
+    hs = (C.c_void_p * n)(*[c.h for c in circuits])
+    out = (C.c_void_p * n)()
+    _check(lib.qt_fuse_many(n, C.cast(hs, C.c_void_p), int(max_fused_qubits), int(threads),
+                            C.cast(out, C.c_void_p)))
+    res = []
+    for c, h in zip(circuits, out):
+        f = Fused.__new__(Fused)
+        f.circuit = c
+        f.h = C.c_void_p(h)
+        res.append(f)
+    return res
+
+
+class Batch:
+    """qt_batch: one trajectory of each fused circuit per run, in one persistent launch."""
+
+    def __init__(self, fused_list):
+        lib = load()
+        self.fused = list(fused_list)
+        n = len(self.fused)
+        hs = (C.c_void_p * n)(*[f.h for f in self.fused])
+        self.h = C.c_void_p()
+        _check(lib.qt_batch_create(n, C.cast(hs, C.c_void_p), C.byref(self.h)))
+        self.num = n
+        self.S = 0
+
+    def run(self, seed=0, first_traj=0, samples_per_traj=0, keep_states=False, use_graph=False,
+            threads=0, stream=None):
+        p = qt_batch_params()
+        p.seed, p.first_traj, p.samples_per_traj = seed, first_traj, samples_per_traj
+        p.keep_states = 1 if keep_states else 0
+        p.use_graph = 1 if use_graph else 0
+        p.threads = threads
+        p.stream = stream
+        _check(load().qt_batch_run(self.h, C.byref(p)))
+        self.S = samples_per_traj
+        return self
+
+    def samples(self):
+        out = np.zeros(max(self.num * self.S, 1), dtype=np.uint64)
+        _check(load().qt_batch_samples(self.h, _ptr(out), len(out)))
+        return out[:self.num * self.S].reshape(self.num, self.S)
+
+    def kraus_indices(self, i):
+        lib = load()
+        nch = C.c_uint32()
+        _check(lib.qt_batch_kraus_indices(self.h, i, None, None, 0, C.byref(nch)))
+        k = np.zeros(max(nch.value, 1), np.int32)
+        st = np.zeros_like(k)
+        _check(lib.qt_batch_kraus_indices(self.h, i, _ptr(k), _ptr(st), len(k), None))
+        return k[:nch.value], st[:nch.value]
+
+    def state(self, i):
+        n = self.fused[i].circuit.num_qubits
+        out = np.zeros(1 << n, dtype=np.complex64)
+        _check(load().qt_batch_state(self.h, i, _ptr(out), out.nbytes))
+        return out
+
+    def stats(self):
+        s = qt_batch_stats_t()
+        _check(load().qt_batch_stats(self.h, C.byref(s)))
+        return {f: getattr(s, f) for f, _ in qt_batch_stats_t._fields_}
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.qt_batch_destroy(self.h)
+            self.h = None
+
+
+def autotune_batch(circuits, sample=256, kmin=2, kmax=4, stream=None):
+    """qt_batch_autotune: returns (best_k, best_threads, {(k, threads): ms})."""
+    lib = load()
+    n = len(circuits)
+    hs = (C.c_void_p * n)(*[c.h for c in circuits])
+    bk, bt = C.c_uint32(), C.c_uint32()
+    table = np.zeros((kmax - kmin + 1) * 3)
+    _check(lib.qt_batch_autotune(n, C.cast(hs, C.c_void_p), sample, kmin, kmax, stream,
+                                 C.byref(bk), C.byref(bt), _ptr(table)))
+    res = {}
+    for k in range(kmin, kmax + 1):
+        for ti, th in enumerate((128, 256, 512)):
+            res[(k, th)] = float(table[(k - kmin) * 3 + ti])
+    return bk.value, bt.value, res

@@ -15,3 +15,5 @@ from .circuits import (  # noqa: F401
     config2_circuit, config3_circuit, serving_requests,
     ghz_circuit, qft_circuit, random_noisy_circuit,
 )
+from .circuits import request_circuit  # noqa: F401,E402
+from .compact import CompactCircuit, layered_compact, config2_compact, request_compact  # noqa: F401,E402

@@ -183,15 +183,11 @@ def random_kraus(d: int, m: int, rng: np.random.Generator) -> np.ndarray:
 # random circuits shaped like the paper's workloads
 # --------------------------------------------------------------------------
 def _one_qubit_layer(rng, n, prev):
-    """One gate per qubit from {sqrtX, sqrtY, sqrtW}, never the previous layer's gate."""
-    choice = np.empty(n, dtype=np.int64)
-    for q in range(n):
-        if prev is None:
-            choice[q] = rng.integers(3)
-        else:
-            others = [g for g in range(3) if g != prev[q]]
-            choice[q] = others[rng.integers(2)]
-    return choice
+    """One gate per qubit from {sqrtX, sqrtY, sqrtW}, never the previous layer's gate:
+    uniform over the three in the first layer, uniform over the other two after."""
+    if prev is None:
+        return rng.integers(3, size=n)
+    return (prev + 1 + rng.integers(2, size=n)) % 3
 
 
 def _grid_couplings(rows, cols, n, layer):

@@ -1,0 +1,124 @@
+"""GPU parity of the batched persistent form.
+
+Every trajectory of a batch (each with its own circuit) is compared with
+the FP64 oracle run of the same circuit, seed and trajectory id (branch
+records where the margin exceeds 1e-6, final state within relative L2
+2e-5 / fidelity 1 - 1e-5, samples where the CDF margin exceeds 1e-6), and
+with the plain per-trajectory loop.  Covers states in shared memory
+(n <= 14) and in global memory (n = 15, 16), forced stage-2 flushes, CUDA
+graph replay, and the autotuner.
+"""
+import numpy as np
+import pytest
+
+import qtsynth as qs
+from gpu_util import MARGIN, STATE_FID, STATE_L2, fidelity, rel_l2, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qt():
+    import paper_2111_02396_gb300 as pkg
+    pkg.load()
+    torch_cuda()
+    return pkg
+
+
+def _workload_circuits(max_n=16, count=20):
+    out, i = [], 0
+    while len(out) < count:
+        cc = qs.config2_compact(i)
+        if cc.num_qubits <= max_n:
+            out.append(cc)
+        i += 1
+    return out
+
+
+def _noisy(n, depth, seed, gamma):
+    rng = np.random.default_rng([0x61, n, seed])
+    return qs.layered_compact(n, depth, rng, lambda l: qs.circuits._chain_couplings(n, l),
+                              dep1=0.02, dep2=0.02, per_gate_ad=gamma)
+
+
+def check_batch(qt, orc, ccs, k, *, seed=0, first=0, S=100, threads=0):
+    qcs = [qt.Circuit.from_compact(c) for c in ccs]
+    fs = qt.fuse_many(qcs, k)
+    b = qt.Batch(fs).run(seed=seed, first_traj=first, samples_per_traj=S, keep_states=True,
+                         threads=threads)
+    smp = b.samples()
+    compared = 0
+    for i, cc in enumerate(ccs):
+        circ = cc.to_circuit()
+        ref = orc.run_trajectory(circ, orc.DELAYED, seed=seed, traj=first + i)
+        kr, st = b.kraus_indices(i)
+        tie = False
+        for ch in range(len(kr)):
+            if ref["margin"][ch] <= MARGIN:
+                tie = True
+                break
+            assert kr[ch] == ref["kraus_idx"][ch], (i, ch)
+            assert st[ch] == ref["stage"][ch], (i, ch)
+        if tie:
+            continue
+        compared += 1
+        g = b.state(i)
+        assert rel_l2(g, ref["state"]) <= STATE_L2, (i, rel_l2(g, ref["state"]))
+        assert fidelity(g, ref["state"]) >= 1 - STATE_FID
+        want, margin = orc.sample(ref["state"], seed, first + i, S)
+        ok = margin > MARGIN
+        np.testing.assert_array_equal(smp[i][ok], want[ok])
+    assert compared >= 0.75 * len(ccs)
+    return b, fs
+
+
+def test_batch_workload_circuits_match_oracle(qt, orc):
+    ccs = _workload_circuits()
+    assert max(c.num_qubits for c in ccs) >= 15          # global-memory states are covered
+    check_batch(qt, orc, ccs, 3)
+
+
+@pytest.mark.parametrize("k", [2, 4])
+def test_batch_forced_flushes(qt, orc, k):
+    ccs = [_noisy(n, 10, s, 0.06) for s, n in enumerate([8, 9, 10, 11, 12, 15])]
+    b, _ = check_batch(qt, orc, ccs, k, seed=3, first=100, S=64, threads=256)
+    assert b.stats()["flushes"] > 0
+
+
+def test_batch_equals_plain_loop(qt):
+    ccs = [_noisy(n, 8, s, 0.03) for s, n in enumerate([8, 10, 12, 13])]
+    qcs = [qt.Circuit.from_compact(c) for c in ccs]
+    fs = qt.fuse_many(qcs, 3)
+    b = qt.Batch(fs).run(seed=9, first_traj=40, samples_per_traj=50)
+    smp = b.samples()
+    for i, f in enumerate(fs):
+        r = qt.Run(f, 1, seed=9, first_traj=40 + i, samples_per_traj=50)
+        kr_plain, _ = r.kraus_indices()
+        kr_b, _ = b.kraus_indices(i)
+        np.testing.assert_array_equal(kr_b, kr_plain[0])
+        # same state up to float rounding: samples agree except near ties
+        assert np.mean(smp[i] == r.samples()[0]) > 0.9
+
+
+def test_batch_graph_replay(qt):
+    torch = torch_cuda()
+    ccs = _workload_circuits(max_n=13, count=12)
+    fs = qt.fuse_many([qt.Circuit.from_compact(c) for c in ccs], 3)
+    b = qt.Batch(fs)
+    s = torch.cuda.Stream()
+    a = b.run(seed=1, first_traj=7, samples_per_traj=32).samples().copy()
+    g1 = b.run(seed=1, first_traj=7, samples_per_traj=32, use_graph=True, stream=s.cuda_stream).samples().copy()
+    g2 = b.run(seed=1, first_traj=7, samples_per_traj=32, use_graph=True, stream=s.cuda_stream).samples().copy()
+    np.testing.assert_array_equal(a, g1)
+    np.testing.assert_array_equal(g1, g2)
+    g3 = b.run(seed=2, first_traj=7, samples_per_traj=32, use_graph=True, stream=s.cuda_stream).samples()
+    assert not np.array_equal(g3, g1)                    # new parameters reach the replayed graph
+
+
+def test_batch_autotuner(qt):
+    ccs = _workload_circuits(max_n=18, count=48)
+    qcs = [qt.Circuit.from_compact(c) for c in ccs]
+    k, threads, table = qt.autotune_batch(qcs, sample=24, kmin=2, kmax=4)
+    assert k in (2, 3, 4) and threads in (128, 256, 512)
+    assert all(v > 0 for v in table.values())
+    assert table[(k, threads)] == min(table.values())
