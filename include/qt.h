@@ -164,6 +164,11 @@ typedef struct {
 } qt_run_stats_t;
 qt_status qt_run_stats(const qt_run* r, qt_run_stats_t* out);
 
+/* <psi|psi> of every final state before normalization (num_traj doubles):
+ * 1 for unitary circuits up to rounding, so |N - 1| is the norm drift of
+ * the arithmetic. */
+qt_status qt_run_norms(const qt_run* r, double* out);
+
 /* Normalized final state of trajectory `traj` (index within the run) as
  * complex64 (re, im float pairs); needs keep_states; dst is host memory of
  * bytes >= 8 * 2^n. */
@@ -267,6 +272,72 @@ void qt_batch_destroy(qt_batch* b);
  * mean ms per run, [(k - kmin) * 3 + {128, 256, 512}]. */
 qt_status qt_batch_autotune(uint32_t num, const qt_circuit* const* circuits, uint32_t sample, uint32_t kmin,
                             uint32_t kmax, void* stream, uint32_t* best_k, uint32_t* best_threads, double* table);
+
+/* ---------------------------------------------------------------------- */
+/* Serving form: a request loop with continuous batching                  */
+/* ---------------------------------------------------------------------- */
+typedef struct {
+  uint64_t budget_bytes;       /* device-memory budget for resident states */
+  uint32_t max_slots;          /* concurrent requests (one stream each), 1..64 */
+  uint32_t small_n_max;        /* batched form for n <= 14, and for n <= this (<= 20) when a
+                                  request has >= 64 trajectories (0: never batched) */
+  uint32_t flags;              /* QT_SERVER_DRY_RUN: no GPU work (scheduling only) */
+} qt_server_config;
+#define QT_SERVER_DRY_RUN 1u
+
+typedef struct {
+  uint64_t seed;               /* Philox key */
+  uint64_t first_traj;         /* trajectory ids first_traj .. first_traj + num_traj - 1 */
+  uint32_t num_traj;
+  uint32_t samples_per_traj;
+} qt_server_request;
+
+typedef struct {
+  int32_t state;               /* 0 queued, 1 running, 2 done, 3 failed, 4 cancelled */
+  int32_t status;              /* qt_status of a finished request */
+  uint32_t attempts;           /* > 1 after a deferral or a requeue */
+  int32_t worker;
+  uint32_t batched;            /* ran in the batched form */
+  uint32_t num_traj, samples_per_traj, pad;
+  uint64_t bytes;              /* admitted footprint */
+  uint64_t flushes;            /* stage-2 channels over its trajectories */
+  double queued_s;             /* submit -> first start */
+  double latency_s;            /* submit -> done (-1 while active) */
+} qt_server_req_info;
+
+typedef struct {
+  uint64_t budget, inflight_bytes, peak_inflight_bytes;
+  uint32_t queued, running, done, failed, workers_alive, requeued, deferred, pad;
+} qt_server_stats_t;
+
+enum { QT_FAULT_WORKER_EXIT = 1, QT_FAULT_ALLOC = 2 };
+
+/* Start max_slots workers, each with its own CUDA stream on the current
+ * device.  A request is admitted in arrival order as soon as a worker is free
+ * and the footprint of the requests in flight plus its own (8 * 2^n bytes per
+ * resident state, Sec. IV.A) fits budget_bytes. */
+qt_status qt_server_create(const qt_server_config* cfg, qt_server** out);
+/* Queue a request; the fused circuit must outlive it.  A request whose
+ * footprint alone exceeds the budget is refused (QT_ERR_OUT_OF_MEMORY). */
+qt_status qt_server_submit(qt_server* s, const qt_fused* f, const qt_server_request* r, uint64_t* id);
+qt_status qt_server_poll(qt_server* s, uint64_t id, int32_t* state);
+/* Block until the request is finished (timeout_ns 0 = no limit). */
+qt_status qt_server_wait(qt_server* s, uint64_t id, uint64_t timeout_ns);
+/* Cancel a request that has not started. */
+qt_status qt_server_cancel(qt_server* s, uint64_t id);
+/* Samples (num_traj * samples_per_traj, trajectory-major) and info of a
+ * request; samples may be NULL to read the info only. */
+qt_status qt_server_result(qt_server* s, uint64_t id, uint64_t* samples, size_t cap, qt_server_req_info* info);
+/* Forget a finished request. */
+qt_status qt_server_release(qt_server* s, uint64_t id);
+qt_status qt_server_stats(qt_server* s, qt_server_stats_t* out);
+/* Host-side fault injection: the next `count` dequeues kill their worker
+ * thread (QT_FAULT_WORKER_EXIT; the watchdog requeues the request and starts
+ * a replacement worker) or fail with an allocation error (QT_FAULT_ALLOC;
+ * the request is deferred and retried). */
+qt_status qt_server_inject(qt_server* s, uint32_t fault, uint32_t count);
+/* Finish running requests, stop the workers and free the server. */
+void qt_server_destroy(qt_server* s);
 
 /* Allocation-free variant of qt_state_reduced_density (no counterpart in the
  * paper: it exists for callers that cannot let a library allocate device

@@ -13,5 +13,5 @@ from .qt import (  # noqa: F401
     Circuit, Fused, Run, QtError, load, lib_path, use_torch_allocator,
     QT_DELAYED, QT_EAGER, QT_FP32, QT_TF32X3,
     qt_state_apply, qt_state_reduced_density, qt_state_sample, qt_state_expect_z,
-    Batch, fuse_many, autotune_batch,
+    Batch, fuse_many, autotune_batch, Server,
 )

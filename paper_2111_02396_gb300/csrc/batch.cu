@@ -46,7 +46,7 @@ constexpr int kSmemNMax = 14;       // states up to 2^14 amplitudes in shared me
 constexpr int kMaxN = 20;           // widest state of the batched form
 
 struct Traj {
-  uint32_t n, gate0, ngates, op0, nops, ch0, nch, pad;
+  uint32_t n, gate0, ngates, op0, nops, ch0, nch, chop0;   // ch0: output offset; chop0: ch_op table offset
   uint64_t arena_off;               // amplitude offset of the kept state (keep_states)
 };
 struct Op {
@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(512) k_batch(const __grid_constant__ Dev d) {
     for (uint64_t x = tid; x < amps; x += blockDim.x) psi[x] = make_float2(x == 0 ? 1.f : 0.f, 0.f);
     // stage 1 of every channel from its draw and the lower bounds
     for (uint32_t c = tid; c < T.nch; c += blockDim.x) {
-      const Op op = d.ops[T.op0 + d.ch_op[T.ch0 + c]];
+      const Op op = d.ops[T.op0 + d.ch_op[T.chop0 + c]];
       const Set st = d.sets[op.set];
       const double r = uniform01(seed, traj_id, kStreamChannel, c);
       const int ch = decide_stage1(st, d.dmat + st.pbar, r);
@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(512) k_batch(const __grid_constant__ Dev d) {
       }
       __syncthreads();
       const int fch = s_next;
-      const uint32_t hi = fch >= 0 ? d.ch_op[T.ch0 + fch] : T.nops;
+      const uint32_t hi = fch >= 0 ? d.ch_op[T.chop0 + fch] : T.nops;
       const int pend_pos = s_pend_pos, pend_choice = s_pend_choice;
       const float pend_scale = s_scale;
       // apply ops [lo, hi): fused gates restricted to the segment
@@ -586,9 +586,23 @@ qt_status qt_batch_create(uint32_t num, const qt_fused* const* fused, qt_batch**
   std::vector<double> dmat;
   std::vector<uint32_t> set_fmat, set_kraus, set_mtm, set_pbar;
   B->traj.resize(num);
+  // a fused circuit that appears several times (e.g. many trajectories of one
+  // request) is packed once; its trajectories share the tables
+  std::unordered_map<const qt_fused*, uint32_t> first_use;
   for (uint32_t i = 0; i < num; ++i) {
     const qt_fused* f = fused[i];
     if (!f) return set_error(QT_ERR_INVALID_ARG, "qt_batch_create: fused %u is NULL", i);
+    auto seen = first_use.find(f);
+    if (seen != first_use.end()) {
+      const bt::Traj& P = B->traj[seen->second];
+      bt::Traj& T = B->traj[i];
+      T = P;
+      T.ch0 = B->total_ch;                 // outputs are per trajectory
+      B->total_ch += T.nch;
+      B->gate_ops += f->gate_ops;
+      continue;
+    }
+    first_use.emplace(f, i);
     const Circuit& c = *f->c;
     if (c.n > static_cast<uint32_t>(bt::kMaxN) || c.n < 1)
       return set_error(QT_ERR_UNSUPPORTED, "qt_batch_create: circuit %u has %u qubits (batched form: 1..%d)", i, c.n,
@@ -598,6 +612,7 @@ qt_status qt_batch_create(uint32_t num, const qt_fused* const* fused, qt_batch**
     T.op0 = static_cast<uint32_t>(ops.size());
     T.nops = static_cast<uint32_t>(c.ops.size());
     T.ch0 = B->total_ch;
+    T.chop0 = static_cast<uint32_t>(ch_op.size());
     T.nch = static_cast<uint32_t>(c.channel_op.size());
     T.gate0 = static_cast<uint32_t>(gates.size());
     T.ngates = static_cast<uint32_t>(f->gates.size());

@@ -264,6 +264,128 @@ static cudaError_t launch_tile(float2* psi, int n, const uint32_t* targets, cons
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// 6-qubit fused gates on CUDA cores (FP32 reference path for the split-TF32
+// tensor-core kernel).  A 64 x 64 complex matrix (32 KB) does not fit in the
+// kernel parameters, so it is staged in shared memory with the tile; each
+// thread computes its set's 64 outputs in blocks of 16 rows, reading the
+// inputs and the (warp-uniform, broadcast) matrix entries from shared memory
+// and writing into a separate output tile.
+// ---------------------------------------------------------------------------
+struct Tile6Args {
+  const float2* u;            // 64 x 64 row-major matrix (device)
+  uint64_t roff[64];
+  uint32_t moff[64];
+  uint32_t tins[6];
+  uint32_t hins[6];
+  int nh, C;
+  uint64_t num_tiles;
+};
+
+constexpr int kTile6Amps = kTileThreads * 64;                      // 8192 amplitudes
+constexpr size_t kTile6Smem = sizeof(float2) * (2 * kTile6Amps + 64 * 64);   // 160 KB
+
+__global__ void __launch_bounds__(kTileThreads, 1) k_apply_tile6(float2* __restrict__ psi,
+                                                                 const __grid_constant__ Tile6Args a) {
+  extern __shared__ __align__(16) float2 sm6[];
+  float2* tin = sm6;
+  float2* tout = sm6 + kTile6Amps;
+  float2* U = sm6 + 2 * kTile6Amps;
+  const uint32_t tid = threadIdx.x;
+  for (int i = tid; i < 64 * 64; i += kTileThreads) U[i] = a.u[i];
+  const uint32_t rowmask = (1u << a.C) - 1u;
+  uint32_t sbase = tid;
+#pragma unroll
+  for (int b = 0; b < 6; ++b) {
+    const uint32_t t = a.tins[b];
+    sbase = ((sbase >> t) << (t + 1)) | (sbase & ((1u << t) - 1u));
+  }
+  const uint64_t tile = blockIdx.x;
+  uint64_t base = tile << a.C;
+  for (int j = 0; j < a.nh; ++j) {
+    const uint32_t h = a.hins[j];
+    base = ((base >> h) << (h + 1)) | (base & ((1ull << h) - 1ull));
+  }
+  for (int i = 0; i < kTile6Amps / 2 / kTileThreads; ++i) {
+    const uint32_t l = 2u * (tid + i * kTileThreads);
+    const uint32_t fl = (l >> 4) & 15u;
+    float4 v = __ldcs(reinterpret_cast<const float4*>(psi + (base | a.roff[l >> a.C] | (l & rowmask))));
+    if (fl & 1u) v = make_float4(v.z, v.w, v.x, v.y);
+    *reinterpret_cast<float4*>(&tin[(l ^ fl) & ~1u]) = v;
+  }
+  __syncthreads();
+  for (int rb = 0; rb < 64; rb += 16) {
+    float xr[16], xi[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) { xr[j] = 0.f; xi[j] = 0.f; }
+    for (int m = 0; m < 64; ++m) {
+      const float2 v = tin[swz(sbase | a.moff[m])];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float2 u = U[(rb + j) * 64 + m];
+        xr[j] = fmaf(u.x, v.x, fmaf(-u.y, v.y, xr[j]));
+        xi[j] = fmaf(u.x, v.y, fmaf(u.y, v.x, xi[j]));
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) tout[swz(sbase | a.moff[rb + j])] = make_float2(xr[j], xi[j]);
+  }
+  __syncthreads();
+  for (int i = 0; i < kTile6Amps / 2 / kTileThreads; ++i) {
+    const uint32_t l = 2u * (tid + i * kTileThreads);
+    const uint32_t fl = (l >> 4) & 15u;
+    float4 v = *reinterpret_cast<const float4*>(&tout[(l ^ fl) & ~1u]);
+    if (fl & 1u) v = make_float4(v.z, v.w, v.x, v.y);
+    __stcs(reinterpret_cast<float4*>(psi + (base | a.roff[l >> a.C] | (l & rowmask))), v);
+  }
+}
+
+cudaError_t launch_apply6_fp32(float2* psi, int n, const uint32_t* targets, const float2* udev, cudaStream_t st) {
+  if (n < 13) return cudaErrorInvalidValue;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = cudaFuncSetAttribute(k_apply_tile6, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(kTile6Smem));
+  });
+  if (attr != cudaSuccess) return attr;
+  Tile6Args a;
+  a.u = udev;
+  int C = 7;
+  for (;;) {
+    int low = 0;
+    for (int b = 0; b < 6; ++b) low += targets[b] < static_cast<uint32_t>(C);
+    if (C - low >= 7) break;
+    ++C;
+  }
+  a.C = C;
+  int nh = 0;
+  uint32_t tpos[6];
+  for (int b = 0; b < 6; ++b) {
+    if (targets[b] < static_cast<uint32_t>(C)) {
+      tpos[b] = targets[b];
+    } else {
+      tpos[b] = static_cast<uint32_t>(C + nh);
+      a.hins[nh++] = targets[b];
+    }
+  }
+  a.nh = nh;
+  for (int b = 0; b < 6; ++b) a.tins[b] = tpos[b];
+  for (int m = 0; m < 64; ++m) {
+    uint32_t o = 0;
+    for (int b = 0; b < 6; ++b)
+      if ((m >> b) & 1) o |= 1u << tpos[b];
+    a.moff[m] = o;
+    uint64_t r = 0;
+    for (int j = 0; j < nh; ++j)
+      if ((m >> j) & 1) r |= 1ull << a.hins[j];
+    a.roff[m] = m < (1 << nh) ? r : 0;
+  }
+  a.num_tiles = 1ull << (n - C - nh);
+  k_apply_tile6<<<static_cast<unsigned>(a.num_tiles), kTileThreads, kTile6Smem, st>>>(psi, a);
+  return cudaGetLastError();
+}
+
 // smallest n for which one tile fits: 7 free bits + k targets
 static inline bool tile_fits(int n, int k) { return n >= 7 + k; }
 

@@ -40,6 +40,8 @@ cudaError_t launch_expect(const float2* psi, int n, int nm, const uint64_t* mask
 // S samples of trajectory traj into out (device)
 cudaError_t launch_sample(const float2* psi, int n, uint64_t seed, uint64_t traj, uint32_t S,
                           uint64_t* out, const Scratch& scr, cudaStream_t st);
+// 6-qubit fused gate on CUDA cores (FP32), matrix 64x64 row-major in device memory, n >= 13
+cudaError_t launch_apply6_fp32(float2* psi, int n, const uint32_t* targets, const float2* udev, cudaStream_t st);
 // tensor-core path (split-TF32, k = 4..6, n >= k + 7): W is the real
 // embedding of U, row-major [2^(k+1) x 2^(k+1)] FP32 in device memory; *err
 // is set (nonzero) if a bounded wait in the kernel ran out

@@ -210,7 +210,16 @@ struct Controller {
               "tensor-core apply kernel launch");
       return QT_OK;
     }
-    if (k > 5) return set_error(QT_ERR_UNSUPPORTED, "fused width %d needs precision QT_TF32X3 (n >= %d)", k, k + 7);
+    if (k == 6 && R.n >= 13) {
+      if (!wbuf.p && (!wbuf.alloc(sizeof(float) * 128 * 128, R.st) || !errbuf.alloc(sizeof(int), R.st)))
+        return set_error(QT_ERR_OUT_OF_MEMORY, "matrix buffer");
+      QT_CUDA(cudaMemcpyAsync(wbuf.p, U, sizeof(float2) * 64 * 64, cudaMemcpyHostToDevice, R.st), "cudaMemcpyAsync(U)");
+      R.stats.h2d_bytes += sizeof(float2) * 64 * 64;
+      QT_CUDA(launch_apply6_fp32(psi, static_cast<int>(R.n), targets.data(), wbuf.as<float2>(), R.st),
+              "6-qubit apply kernel launch");
+      return QT_OK;
+    }
+    if (k > 5) return set_error(QT_ERR_UNSUPPORTED, "fused width %d needs n >= 13", k);
     QT_CUDA(launch_apply(psi, static_cast<int>(R.n), k, targets.data(), U, R.st), "apply kernel launch");
     const size_t d = 1ull << k;
     R.stats.h2d_bytes += sizeof(float2) * d * d;
@@ -455,9 +464,8 @@ qt_status qt_run_trajectories(const qt_fused* f, const qt_run_params* p, qt_run*
   const Circuit& c = *f->c;
   if (c.n < 1) return set_error(QT_ERR_INVALID_ARG, "qt_run_trajectories: empty circuit");
   for (const auto& g : f->gates)
-    if (g.targets.size() > 5 && !(p->precision == QT_TF32X3 && tc_supported(static_cast<int>(c.n), 6)))
-      return set_error(QT_ERR_UNSUPPORTED,
-                       "qt_run_trajectories: fused width %zu needs precision QT_TF32X3 and n >= 13", g.targets.size());
+    if (g.targets.size() > 5 && c.n < 13)
+      return set_error(QT_ERR_UNSUPPORTED, "qt_run_trajectories: fused width %zu needs n >= 13", g.targets.size());
   std::unique_ptr<qt_run> R(new (std::nothrow) qt_run());
   if (!R) return set_error(QT_ERR_OUT_OF_MEMORY, "qt_run_trajectories: host allocation");
   R->f = f;
@@ -592,6 +600,13 @@ qt_status qt_expectation(qt_run* r, uint32_t M, const uint64_t* masks, double* o
   return QT_OK;
 }
 
+qt_status qt_run_norms(const qt_run* r, double* out) {
+  clear_error();
+  if (!r || !out) return set_error(QT_ERR_INVALID_ARG, "qt_run_norms: NULL argument");
+  std::memcpy(out, r->norms.data(), sizeof(double) * r->norms.size());
+  return QT_OK;
+}
+
 qt_status qt_run_state(const qt_run* r, uint32_t t, void* dst, size_t bytes) {
   clear_error();
   if (!r || !dst) return set_error(QT_ERR_INVALID_ARG, "qt_run_state: NULL argument");
@@ -636,9 +651,9 @@ qt_status qt_state_apply(void* state, uint32_t n, uint32_t q, const uint32_t* qu
   clear_error();
   qt_status s = check_state(state, n, "qt_state_apply");
   if (s != QT_OK) return s;
-  const bool tc = precision == QT_TF32X3 && tc_supported(static_cast<int>(n), static_cast<int>(q));
-  if (q < 1 || q > n || q > 6 || (q == 6 && !tc))
-    return set_error(QT_ERR_UNSUPPORTED, "qt_state_apply: q=%u (1..min(n,5); 6 with QT_TF32X3 and n >= 13)", q);
+  const bool tc = precision == QT_TF32X3 && q >= 5 && tc_supported(static_cast<int>(n), static_cast<int>(q));
+  if (q < 1 || q > n || q > 6 || (q == 6 && n < 13))
+    return set_error(QT_ERR_UNSUPPORTED, "qt_state_apply: q=%u (1..min(n,5); 6 needs n >= 13)", q);
   if (precision != QT_FP32 && precision != QT_TF32X3) return set_error(QT_ERR_INVALID_ARG, "qt_state_apply: precision");
   if (!U) return set_error(QT_ERR_INVALID_ARG, "qt_state_apply: U is NULL");
   s = check_qubits(n, q, qubits, "qt_state_apply");
@@ -679,6 +694,15 @@ qt_status qt_state_apply(void* state, uint32_t n, uint32_t q, const uint32_t* qu
     QT_CUDA(cudaMemcpyAsync(&e, ed.p, sizeof(int), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
     QT_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
     if (e) return set_error(QT_ERR_TIMEOUT, "qt_state_apply: tensor-core kernel wait ran out (code %d)", e);
+    return QT_OK;
+  }
+  if (q == 6) {
+    DevBuf ud;
+    if (!ud.alloc(sizeof(float2) * 64 * 64, st)) return set_error(QT_ERR_OUT_OF_MEMORY, "qt_state_apply: matrix buffer");
+    QT_CUDA(cudaMemcpyAsync(ud.p, M.data(), sizeof(float2) * 64 * 64, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
+    QT_CUDA(launch_apply6_fp32(static_cast<float2*>(state), static_cast<int>(n), sorted.data(), ud.as<float2>(), st),
+            "qt_state_apply (6 qubits)");
+    QT_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
     return QT_OK;
   }
   QT_CUDA(launch_apply(static_cast<float2*>(state), static_cast<int>(n), static_cast<int>(q), sorted.data(), M.data(), st),

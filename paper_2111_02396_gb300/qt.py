@@ -74,6 +74,34 @@ class qt_batch_stats_t(C.Structure):
                 ("device_ms", C.c_double)]
 
 
+class qt_server_config(C.Structure):
+    _fields_ = [("budget_bytes", C.c_uint64), ("max_slots", C.c_uint32), ("small_n_max", C.c_uint32),
+                ("flags", C.c_uint32)]
+
+
+class qt_server_request(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("first_traj", C.c_uint64), ("num_traj", C.c_uint32),
+                ("samples_per_traj", C.c_uint32)]
+
+
+class qt_server_req_info(C.Structure):
+    _fields_ = [("state", C.c_int32), ("status", C.c_int32), ("attempts", C.c_uint32), ("worker", C.c_int32),
+                ("batched", C.c_uint32), ("num_traj", C.c_uint32), ("samples_per_traj", C.c_uint32),
+                ("pad", C.c_uint32), ("bytes", C.c_uint64), ("flushes", C.c_uint64),
+                ("queued_s", C.c_double), ("latency_s", C.c_double)]
+
+
+class qt_server_stats_t(C.Structure):
+    _fields_ = [("budget", C.c_uint64), ("inflight_bytes", C.c_uint64), ("peak_inflight_bytes", C.c_uint64),
+                ("queued", C.c_uint32), ("running", C.c_uint32), ("done", C.c_uint32), ("failed", C.c_uint32),
+                ("workers_alive", C.c_uint32), ("requeued", C.c_uint32), ("deferred", C.c_uint32),
+                ("pad", C.c_uint32)]
+
+
+QT_SERVER_DRY_RUN = 1
+QT_FAULT_WORKER_EXIT, QT_FAULT_ALLOC = 1, 2
+
+
 # qt_op as a numpy record (56 bytes, C layout) for vectorized marshalling
 QT_OP_DTYPE = np.dtype({"names": ["kind", "moment", "num_qubits", "qubits", "num_ops", "probs", "mats"],
                         "formats": ["<i4", "<u4", "<u4", ("<u4", 6), "<u4", "<u8", "<u8"],
@@ -86,13 +114,15 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 # every exported symbol of include/qt.h
 EXPORTS = [
     "qt_circuit_create", "qt_fuse", "qt_run_trajectories", "qt_sample", "qt_expectation",
-    "qt_run_kraus_indices", "qt_run_stats", "qt_run_state", "qt_set_allocator",
+    "qt_run_kraus_indices", "qt_run_stats", "qt_run_state", "qt_run_norms", "qt_set_allocator",
     "qt_circuit_destroy", "qt_fused_destroy", "qt_run_destroy", "qt_last_error",
     "qt_fused_info", "qt_fused_gate", "qt_channel_lower_bounds",
     "qt_state_apply", "qt_state_reduced_density", "qt_state_sample", "qt_state_expect_z",
     "qt_state_reduced_density_noalloc",
     "qt_fuse_many", "qt_batch_create", "qt_batch_run", "qt_batch_samples", "qt_batch_kraus_indices",
     "qt_batch_state", "qt_batch_stats", "qt_batch_destroy", "qt_batch_autotune",
+    "qt_server_create", "qt_server_submit", "qt_server_poll", "qt_server_wait", "qt_server_cancel",
+    "qt_server_result", "qt_server_release", "qt_server_stats", "qt_server_inject", "qt_server_destroy",
 ]
 
 _lib = None
@@ -125,6 +155,7 @@ def load(build_if_missing: bool = True):
             "qt_run_kraus_indices": [P, P, P, C.c_size_t],
             "qt_run_stats": [P, P],
             "qt_run_state": [P, u32, P, C.c_size_t],
+            "qt_run_norms": [P, P],
             "qt_set_allocator": [P, P, P],
             "qt_fused_info": [P, P],
             "qt_fused_gate": [P, u32, P, P, P, P, C.c_size_t, P],
@@ -142,12 +173,22 @@ def load(build_if_missing: bool = True):
             "qt_batch_state": [P, u32, P, C.c_size_t],
             "qt_batch_stats": [P, P],
             "qt_batch_autotune": [u32, P, u32, u32, u32, P, P, P, P],
+            "qt_server_create": [P, P],
+            "qt_server_submit": [P, P, P, P],
+            "qt_server_poll": [P, u64, P],
+            "qt_server_wait": [P, u64, u64],
+            "qt_server_cancel": [P, u64],
+            "qt_server_result": [P, u64, P, C.c_size_t, P],
+            "qt_server_release": [P, u64],
+            "qt_server_stats": [P, P],
+            "qt_server_inject": [P, u32, u32],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
             fn.argtypes = args
             fn.restype = C.c_int
-        for name in ("qt_circuit_destroy", "qt_fused_destroy", "qt_run_destroy", "qt_batch_destroy"):
+        for name in ("qt_circuit_destroy", "qt_fused_destroy", "qt_run_destroy", "qt_batch_destroy",
+                     "qt_server_destroy"):
             fn = getattr(lib, name)
             fn.argtypes = [P]
             fn.restype = None
@@ -366,6 +407,11 @@ class Run:
         _check(load().qt_run_stats(self.h, C.byref(s)))
         return {f: getattr(s, f) for f, _ in qt_run_stats_t._fields_}
 
+    def norms(self):
+        out = np.zeros(max(self.num_traj, 1))
+        _check(load().qt_run_norms(self.h, _ptr(out)))
+        return out[:self.num_traj]
+
     def state(self, t):
         n = self.fused.circuit.num_qubits
         out = np.zeros(1 << n, dtype=np.complex64)
@@ -498,3 +544,67 @@ def autotune_batch(circuits, sample=256, kmin=2, kmax=4, stream=None):
         for ti, th in enumerate((128, 256, 512)):
             res[(k, th)] = float(table[(k - kmin) * 3 + ti])
     return bk.value, bt.value, res
+
+
+# ----------------------------------------------------------------------------
+# serving form
+# ----------------------------------------------------------------------------
+class Server:
+    """qt_server: continuous-batching request loop (one stream per slot)."""
+
+    def __init__(self, budget_bytes, max_slots=8, small_n_max=16, dry_run=False):
+        cfg = qt_server_config(int(budget_bytes), int(max_slots), int(small_n_max),
+                               QT_SERVER_DRY_RUN if dry_run else 0)
+        self.h = C.c_void_p()
+        _check(load().qt_server_create(C.byref(cfg), C.byref(self.h)))
+        self._fused = {}
+
+    def submit(self, fused, seed=0, first_traj=0, num_traj=1, samples_per_traj=0):
+        r = qt_server_request(seed, first_traj, num_traj, samples_per_traj)
+        i = C.c_uint64()
+        _check(load().qt_server_submit(self.h, fused.h, C.byref(r), C.byref(i)))
+        self._fused[i.value] = fused          # keep the circuit alive while the request lives
+        return i.value
+
+    def poll(self, rid):
+        st = C.c_int32()
+        _check(load().qt_server_poll(self.h, rid, C.byref(st)))
+        return st.value
+
+    def wait(self, rid, timeout_s=0.0):
+        _check(load().qt_server_wait(self.h, rid, int(timeout_s * 1e9)))
+
+    def cancel(self, rid):
+        _check(load().qt_server_cancel(self.h, rid))
+
+    def info(self, rid):
+        inf = qt_server_req_info()
+        _check(load().qt_server_result(self.h, rid, None, 0, C.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in qt_server_req_info._fields_}
+
+    def result(self, rid):
+        inf = self.info(rid)
+        n = inf["num_traj"] * inf["samples_per_traj"]
+        out = np.zeros(max(n, 1), dtype=np.uint64)
+        _check(load().qt_server_result(self.h, rid, _ptr(out), len(out), None))
+        return out[:n].reshape(inf["num_traj"], inf["samples_per_traj"]), inf
+
+    def release(self, rid):
+        _check(load().qt_server_release(self.h, rid))
+        self._fused.pop(rid, None)
+
+    def stats(self):
+        s = qt_server_stats_t()
+        _check(load().qt_server_stats(self.h, C.byref(s)))
+        return {f: getattr(s, f) for f, _ in qt_server_stats_t._fields_}
+
+    def inject(self, fault, count=1):
+        _check(load().qt_server_inject(self.h, fault, count))
+
+    def close(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.qt_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()

@@ -76,6 +76,21 @@ def test_apply_tf32x3_every_pattern(qt, orc, n, k):
         assert rel_l2(d.cpu().numpy(), want) < TC_L2, (qubits, rel_l2(d.cpu().numpy(), want))
 
 
+@pytest.mark.parametrize("n", [13, 17])
+def test_apply_k6_fp32_every_pattern(qt, orc, n):
+    """6-qubit fused gates on CUDA cores (the FP32 comparator of the TF32x3 path)."""
+    rng = np.random.default_rng([n, 6, 9])
+    for qubits in patterns(n, 6, rng):
+        if max(qubits) >= n:
+            continue
+        U = qs.random_unitary(64, rng)
+        psi = random_state(n, 6)
+        d = to_device(psi)
+        qt.qt_state_apply(d.data_ptr(), n, qubits, U, precision=qt.QT_FP32)
+        want = orc.apply(psi.astype(np.complex128), qubits, U)
+        assert rel_l2(d.cpu().numpy(), want) < KERNEL_L2, (qubits, rel_l2(d.cpu().numpy(), want))
+
+
 def test_apply_sequence_ragged_sizes(qt, orc):
     """Many gates in sequence on sizes that span several grid waves and a
     one-set edge case (n == k)."""

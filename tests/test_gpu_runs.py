@@ -98,6 +98,12 @@ def test_grid20_forced_flushes(qt, orc):
     assert run.stats()["flushes"] == int(np.sum(ref["stage"] == 2))
 
 
+def test_grid_depolarizing_k6_fp32(qt, orc):
+    """The same circuit fused to k = 6 on the FP32 CUDA-core path."""
+    circ = qs.config3_circuit(rows=2, cols=7, depth=12, p=0.02)
+    compare_run(qt, orc, circ, 4, k=6, mode=qt.QT_DELAYED, S=100, precision=qt.QT_FP32)
+
+
 @pytest.mark.parametrize("k", [5, 6])
 def test_grid_depolarizing_tf32x3(qt, orc, k):
     """Depolarizing-only grid circuit (the precision workload's generator at

@@ -1,0 +1,75 @@
+"""GPU checks of the serving loop (continuous batching).
+
+Each request gives the same result served alone as in a mix of concurrent
+requests (bitwise: its work depends only on its own circuit, seed and
+trajectory ids), served small requests match the FP64 oracle (samples where
+the CDF margin exceeds 1e-6), and the in-flight footprint never exceeds the
+budget.
+"""
+import numpy as np
+import pytest
+
+import qtsynth as qs
+from gpu_util import MARGIN, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qt():
+    import paper_2111_02396_gb300 as pkg
+    pkg.load()
+    torch_cuda()
+    return pkg
+
+
+def _requests(qt, count=14, seed=5):
+    reqs = qs.serving_requests(count, seed=seed, nmin=10, nmax=20, dmin=6, dmax=12, tmax=24, samples=20)
+    out = []
+    for r in reqs:
+        f = qt.Fused(qt.Circuit.from_compact(qs.request_compact(r)), 4)
+        out.append((r, f))
+    return out
+
+
+def test_alone_equals_in_mix(qt):
+    reqs = _requests(qt)
+    assert any(r["n"] <= 16 for r, _ in reqs) and any(r["n"] > 16 for r, _ in reqs)
+    budget = 64 << 30
+    mix = qt.Server(budget, max_slots=4, small_n_max=16)
+    ids = [mix.submit(f, seed=r["seed"], first_traj=0, num_traj=r["num_traj"], samples_per_traj=r["samples"])
+           for r, f in reqs]
+    for i in ids:
+        mix.wait(i, timeout_s=300)
+    mixed = [mix.result(i)[0] for i in ids]
+    st = mix.stats()
+    assert st["done"] == len(reqs) and st["peak_inflight_bytes"] <= budget
+    mix.close()
+    alone_srv = qt.Server(budget, max_slots=1, small_n_max=16)
+    for (r, f), m in zip(reqs, mixed):
+        i = alone_srv.submit(f, seed=r["seed"], first_traj=0, num_traj=r["num_traj"],
+                             samples_per_traj=r["samples"])
+        alone_srv.wait(i, timeout_s=300)
+        a, inf = alone_srv.result(i)
+        np.testing.assert_array_equal(a, m)
+    alone_srv.close()
+
+
+def test_served_requests_match_oracle(qt, orc):
+    reqs = [x for x in _requests(qt, count=10, seed=8) if x[0]["n"] <= 13][:3]
+    srv = qt.Server(16 << 30, max_slots=2, small_n_max=16)
+    for r, f in reqs:
+        T = min(r["num_traj"], 6)
+        i = srv.submit(f, seed=r["seed"], first_traj=0, num_traj=T, samples_per_traj=r["samples"])
+        srv.wait(i, timeout_s=300)
+        smp, inf = srv.result(i)
+        assert inf["batched"] == 1
+        circ = qs.request_compact(r).to_circuit()
+        for t in range(T):
+            ref = orc.run_trajectory(circ, orc.DELAYED, seed=r["seed"], traj=t)
+            if np.any(ref["margin"] <= MARGIN):
+                continue
+            want, margin = orc.sample(ref["state"], r["seed"], t, r["samples"])
+            ok = margin > MARGIN
+            np.testing.assert_array_equal(smp[t][ok], want[ok])
+    srv.close()
