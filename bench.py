@@ -468,6 +468,9 @@ def run_serve(args):
     lat_s, t_s, st_s, nb = serve_stream(pkg, fused, reqs, arrivals, slots=args.slots, small_n_max=20,
                                         budget=budget)
     lat_p, t_p, st_p, _ = serve_stream(pkg, fused, reqs, arrivals, slots=1, small_n_max=0, budget=budget)
+    # burst variant: every request arrives at t = 0 (capacity of each form)
+    lat_b, t_b, _, _ = serve_stream(pkg, fused, reqs, [0.0] * R, slots=args.slots, small_n_max=20,
+                                    budget=budget)
     pct = lambda v, q: float(np.percentile(np.asarray(v), q))
     line = {
         "metric": METRIC, "value": total_traj / t_s, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
@@ -482,6 +485,10 @@ def run_serve(args):
         "plain_request_by_request": {"traj_per_s": total_traj / t_p, "p50_s": pct(lat_p, 50),
                                      "p99_s": pct(lat_p, 99), "makespan_s": t_p},
         "speedup_vs_plain": t_p / t_s,
+        "burst": {"served_traj_per_s": total_traj / t_b, "plain_traj_per_s": total_traj / t_cal,
+                  "served_p50_s": pct(lat_b, 50), "served_p99_s": pct(lat_b, 99),
+                  "plain_p50_s": pct(lat, 50), "plain_p99_s": pct(lat, 99),
+                  "capacity_ratio": t_cal / t_b},
         "calibration": {"requests": len(cal), "mean_service_s": mean_service},
     }
     print(json.dumps(line), flush=True)
@@ -553,6 +560,101 @@ def run_precision(args):
     return 0
 
 
+# ----------------------------------------------------------------------------
+# runtime vs noise strength (the shape of the paper's Fig. 3): phase damping
+# after every layer, delayed inner products vs the conventional algorithm
+# ----------------------------------------------------------------------------
+def run_noise_sweep(args):
+    import numpy as np
+    import torch
+
+    import paper_2111_02396_gb300 as pkg
+    import qtsynth as qs
+
+    torch.cuda.set_device(0)
+    pkg.load()
+    sh = torch.cuda.current_stream().cuda_stream
+    lams = [1e-4, 1e-3, 1e-2, 1e-1]
+    table = {}
+    for n, (rows, cols), T in ((20, (4, 5), 8), (27, (3, 9), 4)):
+        rows_out = {}
+        for lam in lams:
+            circ = qs.grid_circuit(rows, cols, 20, 0, layer_pd=lam)
+            f = pkg.Fused(pkg.Circuit.from_synth(circ), 4)
+            entry = {}
+            for name, mode in (("delayed", pkg.QT_DELAYED), ("eager", pkg.QT_EAGER)):
+                pkg.Run(f, 1, seed=1, first_traj=999, mode=mode, stream=sh)        # warm-up
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                t0 = time.perf_counter()
+                e0.record()
+                r = pkg.Run(f, T, seed=1, mode=mode, samples_per_traj=SAMPLES, stream=sh)
+                e1.record()
+                torch.cuda.synchronize()
+                wall = time.perf_counter() - t0
+                st = r.stats()
+                entry[name] = {"ms_per_traj": wall * 1e3 / T, "device_ms_per_traj": e0.elapsed_time(e1) / T,
+                               "prob_passes_per_traj": st["prob_passes"] / T,
+                               "fused_passes_per_traj": st["fused_passes"] / T}
+            entry["eager_over_delayed"] = entry["eager"]["ms_per_traj"] / entry["delayed"]["ms_per_traj"]
+            rows_out[str(lam)] = entry
+        d = np.array([rows_out[str(l)]["delayed"]["ms_per_traj"] for l in lams])
+        slope, icpt = np.polyfit(np.array(lams), d, 1)
+        table[f"n{n}"] = {"lambda": rows_out, "delayed_linear_fit_ms": {"slope_per_unit_lambda": slope,
+                                                                         "intercept": icpt}}
+    line = {"metric": METRIC, "unit": UNIT, "form": "noise-sweep", "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": "grid random circuits depth 20, phase damping lambda per qubit per layer, "
+                                   "fused k=4, 100 samples per trajectory (Fig. 3 shape)"},
+            "sweep": table,
+            "value": table["n27"]["lambda"]["0.0001"]["eager_over_delayed"],
+            "value_meaning": "eager / delayed runtime at n=27, lambda=1e-4 (the paper reports ~10x)"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# small workload: 10-qubit chain, 64 trajectories x 100 samples
+# ----------------------------------------------------------------------------
+def run_chain10(args):
+    import numpy as np
+    import torch
+
+    import paper_2111_02396_gb300 as pkg
+    import qtsynth as qs
+
+    torch.cuda.set_device(0)
+    pkg.load()
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+    circ = qs.config0_circuit()
+    f = pkg.Fused(pkg.Circuit.from_synth(circ), 2)
+    T = 64
+    res = {}
+    for name in ("plain", "batched"):
+        times = []
+        b = pkg.Batch([f] * T) if name == "batched" else None
+        for i in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            if b is None:
+                r = pkg.Run(f, T, seed=0, first_traj=i * T, samples_per_traj=SAMPLES, stream=sh)
+                smp = r.samples()
+            else:
+                smp = b.run(seed=0, first_traj=i * T, samples_per_traj=SAMPLES, use_graph=True,
+                            stream=sh).samples()
+            times.append(time.perf_counter() - t0)
+            assert smp.shape == (T, SAMPLES)
+        t = statistics.median(times[args.warmup:])
+        res[name] = {"traj_per_s": T / t, "ms_per_64_traj": t * 1e3}
+    line = {"metric": METRIC, "value": res["batched"]["traj_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "form": "chain10",
+            "data": "synthetic", "dtype": "f32",
+            "config": {"workload": "chain10: 10-qubit chain, depth 16, depolarizing 1e-3 / 1e-2, amplitude "
+                                   "damping 1e-3, 64 trajectories x 100 samples, fused k=2"},
+            "plain": res["plain"], "batched": res["batched"],
+            "speedup_vs_plain": res["batched"]["traj_per_s"] / res["plain"]["traj_per_s"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -562,7 +664,8 @@ def main():
     ap.add_argument("--traj", type=int, default=16, help="trajectories per step per GPU")
     ap.add_argument("--ref-seconds", type=float, default=15.0, help="oracle sample length")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["grid30", "batch", "serve", "precision"], default="grid30",
+    ap.add_argument("--workload", choices=["grid30", "chain10", "batch", "serve", "precision", "noise-sweep"],
+                    default="grid30",
                     help="grid30: the plain loop at scale (default); batch: the batched form; "
                          "serve: the serving loop")
     ap.add_argument("--requests", type=int, default=120, help="serve: requests of the stream")
@@ -579,6 +682,10 @@ def main():
         return run_serve(args)
     if args.workload == "precision":
         return run_precision(args)
+    if args.workload == "noise-sweep":
+        return run_noise_sweep(args)
+    if args.workload == "chain10":
+        return run_chain10(args)
     return run_ours(args)
 
 

@@ -194,11 +194,11 @@ struct Controller {
   qt_status launch_one(float2* psi, const std::vector<uint32_t>& targets, const float2* U) {
     const int k = static_cast<int>(targets.size());
     if (use_tc(k)) {
-      if (!wbuf.p && (!wbuf.alloc(sizeof(float) * 128 * 128, R.st) || !errbuf.alloc(sizeof(int), R.st)))
+      if (!wbuf.p && !wbuf.alloc(sizeof(float) * 128 * 128, R.st))
         return set_error(QT_ERR_OUT_OF_MEMORY, "tensor-core matrix buffer");
-      if (!err_cleared) {
+      if (!errbuf.p) {                      // device error flag of the tensor-core kernel, cleared once
+        if (!errbuf.alloc(sizeof(int), R.st)) return set_error(QT_ERR_OUT_OF_MEMORY, "error flag");
         QT_CUDA(cudaMemsetAsync(errbuf.p, 0, sizeof(int), R.st), "cudaMemsetAsync");
-        err_cleared = true;
       }
       const int N = 2 << k;
       wtmp.resize(static_cast<size_t>(N) * N);
@@ -211,7 +211,7 @@ struct Controller {
       return QT_OK;
     }
     if (k == 6 && R.n >= 13) {
-      if (!wbuf.p && (!wbuf.alloc(sizeof(float) * 128 * 128, R.st) || !errbuf.alloc(sizeof(int), R.st)))
+      if (!wbuf.p && !wbuf.alloc(sizeof(float) * 128 * 128, R.st))
         return set_error(QT_ERR_OUT_OF_MEMORY, "matrix buffer");
       QT_CUDA(cudaMemcpyAsync(wbuf.p, U, sizeof(float2) * 64 * 64, cudaMemcpyHostToDevice, R.st), "cudaMemcpyAsync(U)");
       R.stats.h2d_bytes += sizeof(float2) * 64 * 64;
@@ -225,7 +225,6 @@ struct Controller {
     R.stats.h2d_bytes += sizeof(float2) * d * d;
     return QT_OK;
   }
-  bool err_cleared = false;
 
   qt_status check_device_error() {
     if (!errbuf.p) return QT_OK;
