@@ -14,21 +14,24 @@
 // in FP32 (the three-pass split-TF32 scheme, Ootomo & Yokota 2022), which
 // leaves only the A_lo B_lo term (~2^-22 relative) out.
 //
-// Data flow (one persistent CTA per SM, 9 warps):
-//   warps 0-3  loaders: thread t owns set t of the tile (TMEM lane t); it
-//              loads its set member by member (a warp reads 32 consecutive
-//              set bases per member: coalesced), splits hi/lo, and writes
-//              A to TMEM with tcgen05.st (A operand taken from TMEM).
+// Data flow (one persistent CTA per SM, 10 warps):
+//   warp 9     producer: stages each tile of 128 gather sets in shared memory
+//              with bulk asynchronous copies (cp.async.bulk, one per row of
+//              2^C >= 128 contiguous amplitudes; the row holds every low
+//              target), completing on a transaction-count mbarrier; two tile
+//              buffers for k <= 5, one for k = 6 (B takes 128 KB);
+//   warps 0-3  converters: thread t owns set t of the tile (TMEM lane t); it
+//              reads its members from the staged tile, splits hi/lo, and
+//              writes A to TMEM with tcgen05.st (A operand taken from TMEM);
 //   warp 8     MMA issuer: one elected thread issues tcgen05.mma (M=128,
 //              N=2^(k+1), K=8 per instruction) with A in TMEM and B in
-//              shared memory, and commits to mbarriers.
-//   warps 4-7  epilogue: tcgen05.ld of the accumulator rows, coalesced
-//              stores of the output sets.
+//              shared memory, and commits to mbarriers;
+//   warps 4-7  epilogue: tcgen05.ld of the accumulator rows, stores of the
+//              output sets (consecutive threads, consecutive sets).
 // TMEM (512 columns): two A slots of 128 columns (hi at +0, lo at +64; one
 // chunk of up to 32 members) and two accumulators of N columns (at 256 and
-// 256 + N), so the loaders fill the
-// next chunk while the tensor core works and the epilogue drains one tile
-// while the next accumulates.
+// 256 + N), so conversion, MMA and draining overlap while the next tile's
+// bytes are in flight.
 //
 // B (hi and lo) is staged once per CTA in shared memory in the K-major
 // no-swizzle layout: core matrices of 8 rows x 16 bytes; adjacent core
@@ -46,7 +49,7 @@ namespace qt {
 
 namespace tc {
 
-constexpr int kThreads = 288;           // 9 warps
+constexpr int kThreads = 320;           // 10 warps
 constexpr int kTileSets = 128;          // M
 constexpr int kMaxChunkReals = 64;      // K per A slot (up to 32 members)
 constexpr uint32_t kTmemCols = 512;
@@ -76,7 +79,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// bounded wait; false on timeout (and *err is set)
+// teardown wait: keeps waiting even after another role has set *err (the
+// operations it waits for are this CTA's own), bounded by the spin limit
+__device__ __forceinline__ bool mbar_drain(uint64_t* bar, uint32_t parity, int* err, int code) {
+  for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    __nanosleep(256);
+  }
+  atomicOr(err, code);
+  return false;
+}
+
+// bounded wait; false on timeout (and *err is set) or when another role has
+// already reported an error
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
   for (uint32_t it = 0; it < kSpinLimit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
@@ -85,6 +100,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
   }
   atomicOr(err, code);
   return false;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// global -> shared bulk copy of `bytes` (16-byte aligned, multiple of 16),
+// completing on `bar`
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
 }
 
 __device__ __forceinline__ void fence_before() {
@@ -163,8 +192,11 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
 
 template <int K>
 struct TcArgs {
-  uint64_t moff[1 << K];     // memory offset of member m within a set
-  uint32_t ins[K];           // ascending target positions (insert zeros)
+  uint64_t roff[1 << K];     // memory offset of tile row r (high-target bits)
+  uint32_t moff[1 << K];     // tile-local offset of member m
+  uint32_t tins[K];          // tile-local target positions, ascending
+  uint32_t hins[K];          // memory positions of the high targets, ascending
+  int nh, C;                 // high targets; contiguous low bits per row
   uint64_t num_tiles;        // tiles of 128 sets
   const float* bmat;         // W row-major [N x N] FP32 (N = 2^(K+1)), device
   int* err;                  // device error flag
@@ -179,22 +211,29 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
   constexpr int CR = N < kMaxChunkReals ? N : kMaxChunkReals;   // reals per A chunk
   constexpr int NCHUNK = N / CR;             // A chunks per tile (1 or 2)
   constexpr int MPC = CR / 2;                // members per chunk (16 or 32)
+  constexpr int TILE_AMPS = kTileSets * NM;
+  constexpr int NBUF = K >= 6 ? 1 : 2;       // staged tiles
   constexpr uint32_t IDESC = idesc_tf32(kTileSets, N);
   extern __shared__ __align__(1024) uint8_t smem[];
   float* bhi = reinterpret_cast<float*>(smem);
   float* blo = bhi + N * N;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(blo + N * N);
+  float2* tbuf = reinterpret_cast<float2*>(blo + N * N);          // NBUF tiles
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tbuf + NBUF * TILE_AMPS);
   uint64_t* a_full = bars;         // [2]
   uint64_t* a_empty = bars + 2;    // [2]
   uint64_t* d_full = bars + 4;     // [2]
   uint64_t* d_empty = bars + 6;    // [2]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 8);
+  uint64_t* t_full = bars + 8;     // [2] tile staged (transaction bytes)
+  uint64_t* t_empty = bars + 10;   // [2] tile read by the converters
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 12);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rowmask = (1u << a.C) - 1u;
+  const uint32_t rowbytes = static_cast<uint32_t>(sizeof(float2)) << a.C;
+  const int nrows = 1 << a.nh;
 
   // stage B = W^T (hi, lo) in the K-major core-matrix layout: element
-  // (n, k) of B^T-as-stored (row n of W, column k) at
-  // (n/8)*SBO + (k/4)*LBO + (n%8)*16 + (k%4)*4
+  // (n, k) of row n of W at (n/8)*SBO + (k/4)*LBO + (n%8)*16 + (k%4)*4
   for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
     const int n = i / N, k = i % N;
     const float w = a.bmat[i];
@@ -210,6 +249,8 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
       mbar_init(&a_empty[i], 1);
       mbar_init(&d_full[i], 1);
       mbar_init(&d_empty[i], 128);
+      mbar_init(&t_full[i], 1);
+      mbar_init(&t_empty[i], 128);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -225,21 +266,44 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tmem_slot;
-  // column map: A slot s at s*128 (hi: +0, lo: +64); accumulator d at 256 + d*N
   const uint32_t a_col0 = 0, d_col0 = 256;
 
-  if (warp < 4) {
-    // ---------------- loaders ----------------
-    const uint32_t lane_base = static_cast<uint32_t>(warp * 32) << 16;
-    uint32_t chunk_iter = 0;
-    for (uint64_t tile = blockIdx.x; tile < a.num_tiles; tile += gridDim.x) {
-      uint64_t base = tile * kTileSets + threadIdx.x;
-#pragma unroll
-      for (int b = 0; b < K; ++b) {
-        const uint32_t s = a.ins[b];
-        base = ((base >> s) << (s + 1)) | (base & ((1ull << s) - 1ull));
+  if (warp == 9) {
+    // ---------------- producer: bulk copies of the tile rows ----------------
+    if (lane == 0) {
+      uint32_t it = 0;
+      for (uint64_t tile = blockIdx.x; tile < a.num_tiles; tile += gridDim.x, ++it) {
+        const uint32_t b = it % NBUF, use = it / NBUF;
+        if (use > 0 && !mbar_wait(&t_empty[b], (use - 1) & 1, a.err, 32)) break;
+        uint64_t base = tile << a.C;
+        for (int j = 0; j < a.nh; ++j) {
+          const uint32_t h = a.hins[j];
+          base = ((base >> h) << (h + 1)) | (base & ((1ull << h) - 1ull));
+        }
+        mbar_expect_tx(&t_full[b], static_cast<uint32_t>(sizeof(float2) * TILE_AMPS));
+        float2* dst = tbuf + b * TILE_AMPS;
+        for (int r = 0; r < nrows; ++r)
+          bulk_g2s(dst + (static_cast<uint32_t>(r) << a.C), psi + (base | a.roff[r]), rowbytes, &t_full[b]);
       }
-      bool ok = true;
+      // no copy may outlive the CTA: wait (bounded) for the last staged tiles
+      for (uint32_t j = it > NBUF ? it - NBUF : 0; j < it; ++j) mbar_drain(&t_full[j % NBUF], (j / NBUF) & 1, a.err, 128);
+    }
+    __syncwarp();
+  } else if (warp < 4) {
+    // ---------------- converters ----------------
+    const uint32_t lane_base = static_cast<uint32_t>(warp * 32) << 16;
+    uint32_t sbase = threadIdx.x;
+#pragma unroll
+    for (int b = 0; b < K; ++b) {
+      const uint32_t t = a.tins[b];
+      sbase = ((sbase >> t) << (t + 1)) | (sbase & ((1u << t) - 1u));
+    }
+    uint32_t chunk_iter = 0, it = 0;
+    bool ok = true;
+    for (uint64_t tile = blockIdx.x; tile < a.num_tiles && ok; tile += gridDim.x, ++it) {
+      const uint32_t b = it % NBUF;
+      if (!mbar_wait(&t_full[b], (it / NBUF) & 1, a.err, 64)) break;
+      const float2* tb = tbuf + b * TILE_AMPS;
       for (int c = 0; c < NCHUNK; ++c, ++chunk_iter) {
         const uint32_t slot = chunk_iter & 1;
         const uint32_t use = chunk_iter >> 1;
@@ -249,7 +313,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
         for (int half = 0; half < MPC / 16; ++half) {
 #pragma unroll
           for (int m = 0; m < 16; ++m) {
-            const float2 v = __ldcs(psi + base + a.moff[c * MPC + half * 16 + m]);
+            const float2 v = tb[sbase | a.moff[c * MPC + half * 16 + m]];
             const uint32_t hr = to_tf32(v.x), hm = to_tf32(v.y);
             hi[2 * m] = hr;
             hi[2 * m + 1] = hm;
@@ -264,23 +328,27 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
         fence_before();
         mbar_arrive(&a_full[slot]);
       }
-      if (!ok) break;
+      mbar_arrive(&t_empty[b]);            // this thread is done reading the staged tile
     }
   } else if (warp < 8) {
     // ---------------- epilogue ----------------
     const int w4 = warp - 4;
     const uint32_t lane_base = static_cast<uint32_t>(w4 * 32) << 16;
-    const uint32_t t_in_tile = static_cast<uint32_t>(w4 * 32 + lane);
+    uint32_t sbase = static_cast<uint32_t>(w4 * 32 + lane);
+#pragma unroll
+    for (int b = 0; b < K; ++b) {
+      const uint32_t t = a.tins[b];
+      sbase = ((sbase >> t) << (t + 1)) | (sbase & ((1u << t) - 1u));
+    }
     uint32_t iter = 0;
     for (uint64_t tile = blockIdx.x; tile < a.num_tiles; tile += gridDim.x, ++iter) {
       const uint32_t db = iter & 1;
       if (!mbar_wait(&d_full[db], (iter >> 1) & 1, a.err, 2)) break;
       fence_after();
-      uint64_t base = tile * kTileSets + t_in_tile;
-#pragma unroll
-      for (int b = 0; b < K; ++b) {
-        const uint32_t s = a.ins[b];
-        base = ((base >> s) << (s + 1)) | (base & ((1ull << s) - 1ull));
+      uint64_t base = tile << a.C;
+      for (int j = 0; j < a.nh; ++j) {
+        const uint32_t h = a.hins[j];
+        base = ((base >> h) << (h + 1)) | (base & ((1ull << h) - 1ull));
       }
 #pragma unroll
       for (int cb = 0; cb < N / 32; ++cb) {
@@ -288,8 +356,11 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
         tmem_ld32(tmem + lane_base + d_col0 + db * N + cb * 32, v);
         tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-          __stcs(psi + base + a.moff[cb * 16 + j], make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1])));
+        for (int j = 0; j < 16; ++j) {
+          const uint32_t l = sbase | a.moff[cb * 16 + j];
+          __stcs(psi + (base | a.roff[l >> a.C] | (l & rowmask)),
+                 make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1])));
+        }
       }
       fence_before();
       mbar_arrive(&d_empty[db]);
@@ -328,9 +399,10 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
       __syncwarp();
     }
   }
-  // teardown: the last commits cover all issued MMAs; the epilogue consumed
-  // every accumulator it waited for.  Wait for in-flight MMAs via a final
-  // commit on a private barrier before freeing TMEM.
+  // teardown: a last commit on a private barrier covers every MMA this CTA
+  // issued; wait for it (bounded) before freeing TMEM.  The producer's copies
+  // have all completed: every staged tile was waited for by the converters,
+  // or the kernel is on its error path after a bounded wait.
   __syncthreads();
   if (warp == 8) {
     __shared__ uint64_t drain;
@@ -340,7 +412,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
       mma_commit(&drain);
     }
     __syncwarp();
-    if (lane == 0) mbar_wait(&drain, 0, a.err, 16);
+    if (lane == 0) mbar_drain(&drain, 0, a.err, 16);
     __syncwarp();
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
@@ -350,8 +422,11 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
 template <int K>
 static cudaError_t launch_tc_k(float2* psi, int n, const uint32_t* targets, const float* wdev, int* err,
                                cudaStream_t st, uint32_t lbo_override, uint32_t sbo_override) {
-  constexpr int N = 2 << K;
-  const size_t smem = 2 * sizeof(float) * N * N + 8 * sizeof(uint64_t) + 16;
+  constexpr int NM = 1 << K;
+  constexpr int N = 2 * NM;
+  constexpr int NBUF = K >= 6 ? 1 : 2;
+  const size_t smem = 2 * sizeof(float) * N * N + NBUF * sizeof(float2) * tc::kTileSets * NM +
+                      12 * sizeof(uint64_t) + 16;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [&] {
@@ -359,14 +434,38 @@ static cudaError_t launch_tc_k(float2* psi, int n, const uint32_t* targets, cons
   });
   if (attr_err != cudaSuccess) return attr_err;
   TcArgs<K> a;
-  for (int m = 0; m < (1 << K); ++m) {
-    uint64_t o = 0;
-    for (int b = 0; b < K; ++b)
-      if ((m >> b) & 1) o |= 1ull << targets[b];
-    a.moff[m] = o;
+  // tile: 2^nh rows of 2^C contiguous amplitudes, C = 7 + targets below C
+  int C = 7;
+  for (;;) {
+    int low = 0;
+    for (int b = 0; b < K; ++b) low += targets[b] < static_cast<uint32_t>(C);
+    if (C - low >= 7) break;
+    ++C;
   }
-  for (int b = 0; b < K; ++b) a.ins[b] = targets[b];
-  a.num_tiles = (1ull << (n - K)) / tc::kTileSets;
+  a.C = C;
+  int nh = 0;
+  uint32_t tpos[K];
+  for (int b = 0; b < K; ++b) {
+    if (targets[b] < static_cast<uint32_t>(C)) {
+      tpos[b] = targets[b];
+    } else {
+      tpos[b] = static_cast<uint32_t>(C + nh);
+      a.hins[nh++] = targets[b];
+    }
+  }
+  a.nh = nh;
+  for (int b = 0; b < K; ++b) a.tins[b] = tpos[b];
+  for (int m = 0; m < NM; ++m) {
+    uint32_t o = 0;
+    for (int b = 0; b < K; ++b)
+      if ((m >> b) & 1) o |= 1u << tpos[b];
+    a.moff[m] = o;
+    uint64_t r = 0;
+    for (int j = 0; j < nh; ++j)
+      if ((m >> j) & 1) r |= 1ull << a.hins[j];
+    a.roff[m] = m < (1 << nh) ? r : 0;
+  }
+  a.num_tiles = 1ull << (n - C - nh);
   a.bmat = wdev;
   a.err = err;
   a.lbo = lbo_override ? lbo_override : 128;
