@@ -58,6 +58,7 @@ typedef enum { QT_OP_GATE = 0, QT_OP_KRAUS = 1, QT_OP_MIXTURE = 2 } qt_op_kind;
 typedef enum { QT_DELAYED = 0, QT_EAGER = 1 } qt_mode;
 typedef enum { QT_FP32 = 0, QT_TF32X3 = 1 } qt_precision;
 #define QT_FLAG_TIME_KERNELS 1u
+#define QT_FLAG_MULTI_GATE 2u    /* group fused gates into multi-gate passes (opt-in) */
 
 #define QT_MAX_QUBITS 34      /* largest state: 2^34 complex64 = 128 GiB */
 #define QT_MAX_OP_QUBITS 6    /* widest gate or channel */
@@ -108,7 +109,8 @@ typedef struct {
   uint32_t num_z_masks;        /* Z-string expectations on each final state */
   const uint64_t* z_masks;     /* num_z_masks masks (copied) */
   uint32_t keep_states;        /* 1: keep every final state on the device */
-  uint32_t flags;              /* QT_FLAG_TIME_KERNELS: time each fused-gate launch */
+  uint32_t flags;              /* QT_FLAG_TIME_KERNELS: time each fused-gate pass;
+                                  QT_FLAG_MULTI_GATE: several fused gates per pass */
   void* stream;                /* cudaStream_t (0 = legacy default stream) */
   uint64_t timeout_ns;         /* bound on any device wait (0 = 10 s) */
 } qt_run_params;
@@ -161,6 +163,8 @@ typedef struct {
   uint64_t h2d_bytes;         /* host->device bytes (copies + matrix parameters) */
   uint64_t d2h_bytes;         /* device->host bytes */
   uint64_t kernel_launches;   /* kernels of this library launched by the run */
+  uint64_t fused_pieces;      /* fused gates (or segment pieces of them) applied; several
+                                 share one pass when a multi-gate pass groups them */
 } qt_run_stats_t;
 qt_status qt_run_stats(const qt_run* r, qt_run_stats_t* out);
 

@@ -136,8 +136,11 @@ struct TileArgs {
 
 __device__ __forceinline__ uint32_t swz(uint32_t l) { return l ^ ((l >> 4) & 15u); }
 
-template <int K>
-__global__ void __launch_bounds__(kTileThreads) k_apply_tile(float2* __restrict__ psi,
+// RU: unroll factor of the row loop.  At K = 4 the rows are fully unrolled
+// (every matrix entry a fixed constant-bank operand) under a 6-CTA occupancy
+// bound (80 registers); for the other widths rows go two at a time.
+template <int K, int RU = 2, int MINB = 1>
+__global__ void __launch_bounds__(kTileThreads, MINB) k_apply_tile(float2* __restrict__ psi,
                                                              const __grid_constant__ TileArgs<K> a) {
   constexpr int M = 1 << K;
   constexpr int TILE = kTileThreads * M;       // amplitudes per tile
@@ -186,10 +189,10 @@ __global__ void __launch_bounds__(kTileThreads) k_apply_tile(float2* __restrict_
       vb[m] = v.y;
       vs[m] = v.x + v.y;
     }
-    // rows two at a time: the matrix entries come in through uniform
-    // constant loads (warp-uniform row index); a full unroll would make the
-    // compiler keep far more values live and spill
-#pragma unroll 2
+    // rows RU at a time: with a partial unroll the matrix entries come in
+    // through uniform constant loads (warp-uniform row index); an unbounded
+    // full unroll makes the compiler keep far more values live
+#pragma unroll RU
     for (int j = 0; j < M; ++j) {
       float t = 0.f, r = 0.f, im = 0.f;
 #pragma unroll
@@ -260,7 +263,10 @@ static cudaError_t launch_tile(float2* psi, int n, const uint32_t* targets, cons
     a.roff[r] = r < (1 << nh) ? o : 0;
   }
   a.num_tiles = 1ull << (n - C - nh);
-  k_apply_tile<K><<<static_cast<unsigned>(a.num_tiles), kTileThreads, 0, st>>>(psi, a);
+  if constexpr (K == 4)
+    k_apply_tile<4, 16, 6><<<static_cast<unsigned>(a.num_tiles), kTileThreads, 0, st>>>(psi, a);
+  else
+    k_apply_tile<K><<<static_cast<unsigned>(a.num_tiles), kTileThreads, 0, st>>>(psi, a);
   return cudaGetLastError();
 }
 
@@ -383,6 +389,213 @@ cudaError_t launch_apply6_fp32(float2* psi, int n, const uint32_t* targets, cons
   }
   a.num_tiles = 1ull << (n - C - nh);
   k_apply_tile6<<<static_cast<unsigned>(a.num_tiles), kTileThreads, kTile6Smem, st>>>(psi, a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Multi-gate pass: several fused gates applied to one tile in shared memory
+// per HBM pass.  The tile holds qubits 0..6 (rows of 128 contiguous
+// amplitudes) and up to 6 higher qubits; every gate of the group acts
+// inside these qubits, so the state is read and written once for the whole
+// group.  Gates are applied in order with a barrier between them; each
+// thread applies its share of the gate's gather sets.
+// ---------------------------------------------------------------------------
+constexpr int kGroupThreads = 256;
+
+struct GroupGate {
+  uint8_t k;                  // width (1..4)
+  uint8_t tins[4];            // tile-local target positions, ascending
+  uint8_t pad[3];
+  uint16_t moff[16];          // tile-local offset of member m
+  uint32_t mat;               // float offset of (c, e, f) in GroupArgs::m
+};
+
+struct GroupArgs {
+  GroupGate g[kGroupMaxGates];
+  float m[kGroupMaxGates * 3 * 256];   // per gate: D*D (e, f) pairs, then D*D c values
+  uint64_t roff[64];                   // memory offset of tile row r
+  uint32_t hins[6];                    // memory positions of the high qubits, ascending
+  int nh, ng;
+  uint32_t nmat;                       // floats of m in use
+  uint64_t num_tiles;
+};
+
+// one gate of a multi-gate pass; its matrix is in shared memory as (e, f)
+// pairs followed by c values (the three-multiply form of k_apply_tile).  A
+// thread applies two gather sets at a time; the (Sum b e, Sum a f) pair is
+// one __ffma2_rn on the swapped member (b, a), and each 128-bit broadcast
+// load (two pairs, or four c values) feeds both sets.
+template <int K, int SPT>
+__device__ __forceinline__ void group_gate(float2* sm, uint32_t tile_amps, const GroupGate G,
+                                           const float* __restrict__ m) {
+  constexpr int M = 1 << K;
+  const uint32_t sets = tile_amps >> K;
+  const float2* ef = reinterpret_cast<const float2*>(m);
+  const float* c = m + 2 * M * M;
+  for (uint32_t s0 = threadIdx.x * SPT; s0 < sets; s0 += kGroupThreads * SPT) {
+    uint32_t bb[SPT];
+    float2 x[SPT][M];
+    float vs[SPT][M];
+#pragma unroll
+    for (int p = 0; p < SPT; ++p) {
+      uint32_t b = s0 + p < sets ? s0 + p : s0;          // sets is even: never clamps in practice
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        const uint32_t t = G.tins[i];
+        b = ((b >> t) << (t + 1)) | (b & ((1u << t) - 1u));
+      }
+      bb[p] = b;
+#pragma unroll
+      for (int j = 0; j < M; ++j) {
+        const float2 v = sm[swz(b | G.moff[j])];
+        x[p][j] = make_float2(v.y, v.x);
+        vs[p][j] = v.x + v.y;
+      }
+    }
+#pragma unroll 2
+    for (int j = 0; j < M; ++j) {
+      float2 pp[SPT];
+      float t[SPT];
+#pragma unroll
+      for (int p = 0; p < SPT; ++p) { pp[p] = make_float2(0.f, 0.f); t[p] = 0.f; }
+      if constexpr (M >= 4) {
+#pragma unroll
+        for (int q = 0; q < M; q += 4) {
+          const float4 e01 = *reinterpret_cast<const float4*>(ef + j * M + q);
+          const float4 e23 = *reinterpret_cast<const float4*>(ef + j * M + q + 2);
+          const float4 cc = *reinterpret_cast<const float4*>(c + j * M + q);
+          const float2 ev[4] = {make_float2(e01.x, e01.y), make_float2(e01.z, e01.w), make_float2(e23.x, e23.y),
+                                make_float2(e23.z, e23.w)};
+          const float cv[4] = {cc.x, cc.y, cc.z, cc.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int p = 0; p < SPT; ++p) {
+              pp[p] = __ffma2_rn(ev[u], x[p][q + u], pp[p]);
+              t[p] = fmaf(cv[u], vs[p][q + u], t[p]);
+            }
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < M; ++q)
+#pragma unroll
+          for (int p = 0; p < SPT; ++p) {
+            pp[p] = __ffma2_rn(ef[j * M + q], x[p][q], pp[p]);
+            t[p] = fmaf(c[j * M + q], vs[p][q], t[p]);
+          }
+      }
+#pragma unroll
+      for (int p = 0; p < SPT; ++p)
+        if (s0 + p < sets) sm[swz(bb[p] | G.moff[j])] = make_float2(t[p] - pp[p].x, t[p] + pp[p].y);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kGroupThreads, 2) k_apply_group(float2* __restrict__ psi,
+                                                               const __grid_constant__ GroupArgs a) {
+  extern __shared__ __align__(16) float2 smg[];
+  const uint32_t tid = threadIdx.x;
+  const uint32_t tile_amps = 128u << a.nh;
+  float* smat = reinterpret_cast<float*>(smg + tile_amps);     // the group's matrices
+  const uint64_t tile = blockIdx.x;
+  uint64_t base = tile << 7;
+  for (int j = 0; j < a.nh; ++j) {
+    const uint32_t h = a.hins[j];
+    base = ((base >> h) << (h + 1)) | (base & ((1ull << h) - 1ull));
+  }
+  for (uint32_t i = tid; i < a.nmat; i += kGroupThreads) smat[i] = a.m[i];
+  for (uint32_t c = tid; c < tile_amps / 2; c += kGroupThreads) {
+    const uint32_t l = 2u * c;
+    const uint32_t fl = (l >> 4) & 15u;
+    float4 v = __ldcs(reinterpret_cast<const float4*>(psi + (base | a.roff[l >> 7] | (l & 127u))));
+    if (fl & 1u) v = make_float4(v.z, v.w, v.x, v.y);
+    *reinterpret_cast<float4*>(&smg[(l ^ fl) & ~1u]) = v;
+  }
+  for (int gi = 0; gi < a.ng; ++gi) {
+    __syncthreads();
+    const GroupGate G = a.g[gi];            // descriptor in registers
+    const float* m = smat + G.mat;
+    switch (G.k) {
+      case 1: group_gate<1, 2>(smg, tile_amps, G, m); break;
+      case 2: group_gate<2, 2>(smg, tile_amps, G, m); break;
+      case 3: group_gate<3, 2>(smg, tile_amps, G, m); break;
+      default: group_gate<4, 2>(smg, tile_amps, G, m); break;
+    }
+  }
+  __syncthreads();
+  for (uint32_t c = tid; c < tile_amps / 2; c += kGroupThreads) {
+    const uint32_t l = 2u * c;
+    const uint32_t fl = (l >> 4) & 15u;
+    float4 v = *reinterpret_cast<const float4*>(&smg[(l ^ fl) & ~1u]);
+    if (fl & 1u) v = make_float4(v.z, v.w, v.x, v.y);
+    __stcs(reinterpret_cast<float4*>(psi + (base | a.roff[l >> 7] | (l & 127u))), v);
+  }
+}
+
+cudaError_t launch_apply_group(float2* psi, int n, int ng, const GroupPiece* pieces, cudaStream_t st) {
+  if (ng < 1 || ng > kGroupMaxGates) return cudaErrorInvalidValue;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = cudaFuncSetAttribute(k_apply_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>((sizeof(float2) << 13) + sizeof(float) * kGroupMaxGates * 3 * 256));
+  });
+  if (attr != cudaSuccess) return attr;
+  GroupArgs a;
+  // high qubits of the group (>= 7), ascending
+  uint32_t hmask = 0;
+  for (int gi = 0; gi < ng; ++gi)
+    for (int b = 0; b < pieces[gi].k; ++b)
+      if (pieces[gi].targets[b] >= 7) hmask |= 1u << (pieces[gi].targets[b] - 7);
+  int nh = 0;
+  for (int q = 0; q < 32; ++q)
+    if (hmask & (1u << q)) {
+      if (nh == 6) return cudaErrorInvalidValue;
+      a.hins[nh++] = static_cast<uint32_t>(q + 7);
+    }
+  if (n < 7 + nh) return cudaErrorInvalidValue;
+  a.nh = nh;
+  a.ng = ng;
+  auto tpos = [&](uint32_t q) -> uint32_t {
+    if (q < 7) return q;
+    for (int j = 0; j < nh; ++j)
+      if (a.hins[j] == q) return static_cast<uint32_t>(7 + j);
+    return 0;
+  };
+  uint32_t off = 0;
+  for (int gi = 0; gi < ng; ++gi) {
+    const GroupPiece& P = pieces[gi];
+    GroupGate& G = a.g[gi];
+    const int K = P.k, M = 1 << K;
+    G.k = static_cast<uint8_t>(K);
+    uint32_t pos[4];
+    for (int b = 0; b < K; ++b) pos[b] = tpos(P.targets[b]);
+    for (int b = 0; b < K; ++b) G.tins[b] = static_cast<uint8_t>(pos[b]);   // targets ascending -> positions ascending
+    for (int j = 0; j < 16; ++j) {
+      uint32_t o = 0;
+      for (int b = 0; b < K; ++b)
+        if ((j >> b) & 1) o |= 1u << pos[b];
+      G.moff[j] = static_cast<uint16_t>(j < M ? o : 0);
+    }
+    G.mat = off;
+    for (int j = 0; j < M * M; ++j) {          // (e, f) pairs, then c
+      const float re = P.u[j].x, im = P.u[j].y;
+      a.m[off + 2 * j] = re + im;
+      a.m[off + 2 * j + 1] = im - re;
+      a.m[off + 2 * M * M + j] = re;
+    }
+    off += 3 * M * M;
+  }
+  for (int r = 0; r < 64; ++r) {
+    uint64_t o = 0;
+    for (int j = 0; j < nh; ++j)
+      if ((r >> j) & 1) o |= 1ull << a.hins[j];
+    a.roff[r] = r < (1 << nh) ? o : 0;
+  }
+  a.nmat = off;
+  a.num_tiles = 1ull << (n - 7 - nh);
+  const size_t smem = (sizeof(float2) << (7 + nh)) + sizeof(float) * off;
+  k_apply_group<<<static_cast<unsigned>(a.num_tiles), kGroupThreads, smem, st>>>(psi, a);
   return cudaGetLastError();
 }
 

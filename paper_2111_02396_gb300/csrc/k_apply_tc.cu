@@ -18,8 +18,9 @@
 //   warp 9     producer: stages each tile of 128 gather sets in shared memory
 //              with bulk asynchronous copies (cp.async.bulk, one per row of
 //              2^C >= 128 contiguous amplitudes; the row holds every low
-//              target), completing on a transaction-count mbarrier; two tile
-//              buffers for k <= 5, one for k = 6 (B takes 128 KB);
+//              target), completing on a transaction-count mbarrier; 8 tile
+//              buffers for k = 4, 4 for k = 5, and for k = 6 (B takes 128 KB)
+//              one buffer staged as two chunk halves;
 //   warps 0-3  converters: thread t owns set t of the tile (TMEM lane t); it
 //              reads its members from the staged tile, splits hi/lo, and
 //              writes A to TMEM with tcgen05.st (A operand taken from TMEM);
@@ -212,7 +213,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
   constexpr int NCHUNK = N / CR;             // A chunks per tile (1 or 2)
   constexpr int MPC = CR / 2;                // members per chunk (16 or 32)
   constexpr int TILE_AMPS = kTileSets * NM;
-  constexpr int NBUF = K >= 6 ? 1 : 2;       // staged tiles
+  constexpr int NBUF = K >= 6 ? 1 : (K == 5 ? 4 : 8);   // staged tiles (bytes in flight)
   constexpr uint32_t IDESC = idesc_tf32(kTileSets, N);
   extern __shared__ __align__(1024) uint8_t smem[];
   float* bhi = reinterpret_cast<float*>(smem);
@@ -223,9 +224,9 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
   uint64_t* a_empty = bars + 2;    // [2]
   uint64_t* d_full = bars + 4;     // [2]
   uint64_t* d_empty = bars + 6;    // [2]
-  uint64_t* t_full = bars + 8;     // [2] tile staged (transaction bytes)
-  uint64_t* t_empty = bars + 10;   // [2] tile read by the converters
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 12);
+  uint64_t* t_full = bars + 8;     // [8] tile staged (transaction bytes)
+  uint64_t* t_empty = bars + 16;   // [8] tile read by the converters
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 24);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rowmask = (1u << a.C) - 1u;
@@ -249,6 +250,8 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
       mbar_init(&a_empty[i], 1);
       mbar_init(&d_full[i], 1);
       mbar_init(&d_empty[i], 128);
+    }
+    for (int i = 0; i < 8; ++i) {
       mbar_init(&t_full[i], 1);
       mbar_init(&t_empty[i], 128);
     }
@@ -268,25 +271,44 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
   const uint32_t tmem = *tmem_slot;
   const uint32_t a_col0 = 0, d_col0 = 256;
 
+  // k = 6: when the top target is a high qubit, chunk c of a tile is exactly
+  // the half of its rows whose top row bit is c, so the two halves of the
+  // single tile buffer are staged and released independently
+  const bool split = NCHUNK == 2 && a.nh >= 1 && a.tins[K - 1] == static_cast<uint32_t>(a.C + a.nh - 1);
   if (warp == 9) {
     // ---------------- producer: bulk copies of the tile rows ----------------
     if (lane == 0) {
+      uint32_t lastuse[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      int issued[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      // stage units: whole tiles (two buffers), or for k = 6 with a high top
+      // target the two chunk halves of one tile buffer
       uint32_t it = 0;
-      for (uint64_t tile = blockIdx.x; tile < a.num_tiles; tile += gridDim.x, ++it) {
-        const uint32_t b = it % NBUF, use = it / NBUF;
-        if (use > 0 && !mbar_wait(&t_empty[b], (use - 1) & 1, a.err, 32)) break;
+      const int nunits = split ? 2 : 1;
+      const int urows = nrows / nunits;
+      const uint32_t ubytes = static_cast<uint32_t>(sizeof(float2) * TILE_AMPS) / nunits;
+      bool stop = false;
+      for (uint64_t tile = blockIdx.x; tile < a.num_tiles && !stop; tile += gridDim.x, ++it) {
         uint64_t base = tile << a.C;
         for (int j = 0; j < a.nh; ++j) {
           const uint32_t h = a.hins[j];
           base = ((base >> h) << (h + 1)) | (base & ((1ull << h) - 1ull));
         }
-        mbar_expect_tx(&t_full[b], static_cast<uint32_t>(sizeof(float2) * TILE_AMPS));
-        float2* dst = tbuf + b * TILE_AMPS;
-        for (int r = 0; r < nrows; ++r)
-          bulk_g2s(dst + (static_cast<uint32_t>(r) << a.C), psi + (base | a.roff[r]), rowbytes, &t_full[b]);
+        for (int u = 0; u < nunits; ++u) {
+          const uint32_t b = split ? static_cast<uint32_t>(u) : it % NBUF;
+          const uint32_t use = split ? it : it / NBUF;
+          if (use > 0 && !mbar_wait(&t_empty[b], (use - 1) & 1, a.err, 32)) { stop = true; break; }
+          mbar_expect_tx(&t_full[b], ubytes);
+          float2* dst = split ? tbuf + u * (TILE_AMPS / 2) : tbuf + b * TILE_AMPS;
+          for (int r = 0; r < urows; ++r)
+            bulk_g2s(dst + (static_cast<uint32_t>(r) << a.C), psi + (base | a.roff[u * urows + r]), rowbytes,
+                     &t_full[b]);
+          lastuse[b] = use;
+          issued[b] = 1;
+        }
       }
-      // no copy may outlive the CTA: wait (bounded) for the last staged tiles
-      for (uint32_t j = it > NBUF ? it - NBUF : 0; j < it; ++j) mbar_drain(&t_full[j % NBUF], (j / NBUF) & 1, a.err, 128);
+      // no copy may outlive the CTA: wait (bounded) for the last staged units
+      for (int b = 0; b < 8; ++b)
+        if (issued[b]) mbar_drain(&t_full[b], lastuse[b] & 1, a.err, 128);
     }
     __syncwarp();
   } else if (warp < 4) {
@@ -301,10 +323,11 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
     uint32_t chunk_iter = 0, it = 0;
     bool ok = true;
     for (uint64_t tile = blockIdx.x; tile < a.num_tiles && ok; tile += gridDim.x, ++it) {
-      const uint32_t b = it % NBUF;
-      if (!mbar_wait(&t_full[b], (it / NBUF) & 1, a.err, 64)) break;
+      const uint32_t b = split ? 0u : it % NBUF;
+      if (!split && !mbar_wait(&t_full[b], (it / NBUF) & 1, a.err, 64)) break;
       const float2* tb = tbuf + b * TILE_AMPS;
       for (int c = 0; c < NCHUNK; ++c, ++chunk_iter) {
+        if (split && !mbar_wait(&t_full[c], it & 1, a.err, 64)) { ok = false; break; }
         const uint32_t slot = chunk_iter & 1;
         const uint32_t use = chunk_iter >> 1;
         if (use > 0 && !mbar_wait(&a_empty[slot], (use - 1) & 1, a.err, 1)) { ok = false; break; }
@@ -327,8 +350,9 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
         tmem_wait_st();
         fence_before();
         mbar_arrive(&a_full[slot]);
+        if (split) mbar_arrive(&t_empty[c]);   // done reading this chunk's half
       }
-      mbar_arrive(&t_empty[b]);            // this thread is done reading the staged tile
+      if (!split && ok) mbar_arrive(&t_empty[b]);   // done reading the staged tile
     }
   } else if (warp < 8) {
     // ---------------- epilogue ----------------
@@ -424,9 +448,9 @@ static cudaError_t launch_tc_k(float2* psi, int n, const uint32_t* targets, cons
                                cudaStream_t st, uint32_t lbo_override, uint32_t sbo_override) {
   constexpr int NM = 1 << K;
   constexpr int N = 2 * NM;
-  constexpr int NBUF = K >= 6 ? 1 : 2;
+  constexpr int NBUF = K >= 6 ? 1 : (K == 5 ? 4 : 8);
   const size_t smem = 2 * sizeof(float) * N * N + NBUF * sizeof(float2) * tc::kTileSets * NM +
-                      12 * sizeof(uint64_t) + 16;
+                      24 * sizeof(uint64_t) + 16;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [&] {

@@ -42,6 +42,17 @@ cudaError_t launch_sample(const float2* psi, int n, uint64_t seed, uint64_t traj
                           uint64_t* out, const Scratch& scr, cudaStream_t st);
 // 6-qubit fused gate on CUDA cores (FP32), matrix 64x64 row-major in device memory, n >= 13
 cudaError_t launch_apply6_fp32(float2* psi, int n, const uint32_t* targets, const float2* udev, cudaStream_t st);
+// multi-gate pass: up to kGroupMaxGates fused gates (width <= 4, targets
+// ascending, matrix row-major) whose qubits lie in {0..6} plus at most 6
+// higher qubits, applied in one pass over the state (n >= 7 + #high qubits)
+constexpr int kGroupMaxGates = 8;
+constexpr int kGroupMaxHigh = 6;
+struct GroupPiece {
+  int k;
+  uint32_t targets[4];
+  const float2* u;
+};
+cudaError_t launch_apply_group(float2* psi, int n, int ng, const GroupPiece* pieces, cudaStream_t st);
 // tensor-core path (split-TF32, k = 4..6, n >= k + 7): W is the real
 // embedding of U, row-major [2^(k+1) x 2^(k+1)] FP32 in device memory; *err
 // is set (nonzero) if a bounded wait in the kernel ran out

@@ -17,7 +17,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <bit>
 #include <cmath>
+#include <deque>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -235,7 +237,9 @@ struct Controller {
     return QT_OK;
   }
 
-  qt_status apply(float2* psi, const std::vector<uint32_t>& targets, const float2* U) {
+  // one pass over the state, optionally bracketed by timing events
+  template <typename F>
+  qt_status timed_launch(F&& launch, const char* what) {
     const bool timed = (R.p.flags & QT_FLAG_TIME_KERNELS) != 0;
     if (timed) {
       if (ev_used + 2 > ev.size()) {
@@ -247,8 +251,10 @@ struct Controller {
       }
       QT_CUDA(cudaEventRecord(ev[ev_used], R.st), "cudaEventRecord");
     }
-    qt_status ls = launch_one(psi, targets, U);
+    cudaError_t e = cudaSuccess;
+    qt_status ls = launch(e);
     if (ls != QT_OK) return ls;
+    if (e != cudaSuccess) return cuda_fail(e, what);
     if (timed) {
       QT_CUDA(cudaEventRecord(ev[ev_used + 1], R.st), "cudaEventRecord");
       ev_used += 2;
@@ -257,6 +263,10 @@ struct Controller {
     R.stats.kernel_launches++;
     R.stats.apply_bytes += 16ull << R.n;
     return QT_OK;
+  }
+
+  qt_status apply(float2* psi, const std::vector<uint32_t>& targets, const float2* U) {
+    return timed_launch([&](cudaError_t&) { return launch_one(psi, targets, U); }, "apply kernel launch");
   }
 
   qt_status collect_timing() {
@@ -273,6 +283,14 @@ struct Controller {
     return QT_OK;
   }
 
+  // one piece of a segment: a fused gate restricted to the segment's ops
+  struct Piece {
+    std::vector<uint32_t> targets;
+    const float2* u;
+    uint64_t full;                    // qubit mask
+  };
+  std::deque<std::vector<float2>> owned;
+
   // Apply ops [lo, hi) of the circuit.  choice[ch] is the operator of each
   // channel; norm_scale[ch] > 0 marks a stage-2 choice applied as
   // K_i * norm_scale (the Kraus form, normalized).
@@ -280,6 +298,8 @@ struct Controller {
                         const std::vector<double>& norm_scale) {
     std::vector<std::pair<uint32_t, const cd*>> seq;
     std::vector<std::vector<cd>> scaled;
+    std::vector<Piece> pieces;
+    owned.clear();
     for (size_t g = 0; g < f.gates.size(); ++g) {
       const FusedGate& fg = f.gates[g];
       seq.clear();
@@ -312,17 +332,76 @@ struct Controller {
       for (auto& e : seq)
         if (!e.second) e.second = scaled[si++].data();
       if (whole && dflt) {
-        qt_status s = apply(psi, fg.targets, def32[g].data());
-        if (s != QT_OK) return s;
+        uint64_t fm = 0;
+        for (uint32_t q : fg.targets) fm |= 1ull << q;
+        pieces.push_back(Piece{fg.targets, def32[g].data(), fm});
         continue;
       }
       std::vector<uint32_t> targets;
       for (uint32_t q = 0; q < 64; ++q)
         if (mask & (1ull << q)) targets.push_back(q);
       compose(c, targets, seq, tmp);
-      to_f32(tmp, tmp32);
-      qt_status s = apply(psi, targets, tmp32.data());
+      owned.emplace_back();
+      to_f32(tmp, owned.back());
+      pieces.push_back(Piece{targets, owned.back().data(), mask});
+    }
+    return launch_pieces(psi, pieces);
+  }
+
+  // Launch the pieces of a segment in order.  With QT_FLAG_MULTI_GATE, consecutive
+  // pieces (moved earlier past pieces they share no qubit with) whose qubits
+  // lie in {0..6} plus at most kGroupMaxHigh higher qubits share one
+  // multi-gate pass over the state.
+  qt_status launch_pieces(float2* psi, const std::vector<Piece>& pieces) {
+    const bool group = (R.p.flags & QT_FLAG_MULTI_GATE) && R.n >= 8;
+    const int hmax = std::min<int>(kGroupMaxHigh, static_cast<int>(R.n) - 7);
+    const uint64_t low = (1ull << 7) - 1ull;
+    std::vector<char> done(pieces.size(), 0);
+    std::vector<size_t> members;
+    for (size_t a = 0; a < pieces.size(); ++a) {
+      if (done[a]) continue;
+      done[a] = 1;
+      members.assign(1, a);
+      const int wa = static_cast<int>(pieces[a].targets.size());
+      const bool groupable_a = group && wa <= 4 && !use_tc(wa) &&
+                               std::popcount(pieces[a].full & ~low) <= hmax;
+      if (groupable_a) {
+        uint64_t hm = pieces[a].full & ~low, blocked = 0;
+        for (size_t b = a + 1; b < pieces.size() && b < a + 64 &&
+                               members.size() < static_cast<size_t>(kGroupMaxGates); ++b) {
+          if (done[b]) continue;
+          const Piece& P = pieces[b];
+          const int wb = static_cast<int>(P.targets.size());
+          if ((P.full & blocked) == 0 && wb <= 4 && std::popcount(hm | (P.full & ~low)) <= hmax) {
+            hm |= P.full & ~low;
+            members.push_back(b);
+            done[b] = 1;
+            continue;
+          }
+          blocked |= P.full;
+        }
+      }
+      if (members.size() == 1) {
+        qt_status s = apply(psi, pieces[a].targets, pieces[a].u);
+        if (s != QT_OK) return s;
+        R.stats.fused_pieces++;
+        continue;
+      }
+      GroupPiece gp[kGroupMaxGates];
+      for (size_t i = 0; i < members.size(); ++i) {
+        const Piece& P = pieces[members[i]];
+        gp[i].k = static_cast<int>(P.targets.size());
+        for (size_t b = 0; b < P.targets.size(); ++b) gp[i].targets[b] = P.targets[b];
+        gp[i].u = P.u;
+        const size_t d = 1ull << P.targets.size();
+        R.stats.h2d_bytes += sizeof(float2) * d * d;
+      }
+      qt_status s = timed_launch([&](cudaError_t& e) {
+        e = launch_apply_group(psi, static_cast<int>(R.n), static_cast<int>(members.size()), gp, R.st);
+        return QT_OK;
+      }, "multi-gate pass launch");
       if (s != QT_OK) return s;
+      R.stats.fused_pieces += members.size();
     }
     return QT_OK;
   }

@@ -40,7 +40,13 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--reads", action="store_true", help="also time the read passes")
     ap.add_argument("--tf32", action="store_true", help="split-TF32 tensor-core path (k = 4..6)")
+    ap.add_argument("--grid", type=int, nargs=2, metavar=("ROWS", "COLS"),
+                    help="instead: time whole trajectories of the damped grid workload on a ROWS x COLS grid")
+    ap.add_argument("--fuse", type=int, default=4, help="--grid: fusion width")
+    ap.add_argument("--grouping", action="store_true", help="--grid: multi-gate passes")
     args = ap.parse_args(argv)
+    if args.grid:
+        return grid_runs(args)
     pkg.load()
     n = args.n
     st = torch.cuda.current_stream()
@@ -82,6 +88,32 @@ def main(argv=None):
         print(json.dumps(dict(kernel="expect16", n=n, ms=ms, gbs=gbs)), flush=True)
         ms, gbs = timeit(lambda: pkg.qt_state_sample(d.data_ptr(), n, 0, 0, 100, stream=st.cuda_stream), 8 << n)
         print(json.dumps(dict(kernel="sample100", n=n, ms=ms, gbs=gbs)), flush=True)
+
+
+def grid_runs(args):
+    """Whole trajectories (all kernels of the plain loop) on a smaller grid."""
+    import torch
+
+    import paper_2111_02396_gb300 as pkg
+    import qtsynth as qs
+    pkg.load()
+    rows, cols = args.grid
+    n = rows * cols
+    circ = qs.config1_circuit(rows=rows, cols=cols)
+    f = pkg.Fused(pkg.Circuit.from_synth(circ), args.fuse)
+    sh = torch.cuda.current_stream().cuda_stream
+    for i in range(args.warmup):
+        pkg.Run(f, 1, seed=0, first_traj=100 + i, grouping=args.grouping, stream=sh)
+    torch.cuda.synchronize()
+    r = pkg.Run(f, args.reps, seed=0, time_kernels=True, grouping=args.grouping, stream=sh)
+    st = r.stats()
+    row = dict(kernel="grid_run", n=n, fuse=args.fuse, grouping=args.grouping, traj=args.reps,
+               ms_per_traj=st["device_ms"] / args.reps, passes_per_traj=st["fused_passes"] / args.reps,
+               pieces_per_traj=st["fused_pieces"] / args.reps,
+               pass_gbs=st["apply_bytes"] / (st["apply_ms"] / 1e3) / 1e9 if st["apply_ms"] else None,
+               gate_equiv_gbs=(st["fused_pieces"] * 16 * (1 << n)) / (st["apply_ms"] / 1e3) / 1e9
+               if st["apply_ms"] else None)
+    print(json.dumps(row), flush=True)
 
 
 if __name__ == "__main__":

@@ -27,6 +27,7 @@ QT_OP_GATE, QT_OP_KRAUS, QT_OP_MIXTURE = 0, 1, 2
 QT_DELAYED, QT_EAGER = 0, 1
 QT_FP32, QT_TF32X3 = 0, 1
 QT_FLAG_TIME_KERNELS = 1
+QT_FLAG_MULTI_GATE = 2
 
 
 class QtError(RuntimeError):
@@ -54,7 +55,7 @@ class qt_run_stats_t(C.Structure):
                 ("gate_ops", C.c_uint64), ("flushes", C.c_uint64),
                 ("device_ms", C.c_double), ("apply_ms", C.c_double),
                 ("apply_bytes", C.c_uint64), ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64),
-                ("kernel_launches", C.c_uint64)]
+                ("kernel_launches", C.c_uint64), ("fused_pieces", C.c_uint64)]
 
 
 class qt_fused_info_t(C.Structure):
@@ -364,7 +365,7 @@ class Fused:
 class Run:
     def __init__(self, fused: Fused, num_traj, *, seed=0, first_traj=0, mode=QT_DELAYED,
                  precision=QT_FP32, samples_per_traj=0, z_masks=(), keep_states=False,
-                 time_kernels=False, stream=None):
+                 time_kernels=False, grouping=False, stream=None):
         lib = load()
         self.fused = fused
         self.masks = np.ascontiguousarray(np.asarray(z_masks, dtype=np.uint64))
@@ -374,7 +375,7 @@ class Run:
         p.num_z_masks = len(self.masks)
         p.z_masks = self.masks.ctypes.data if len(self.masks) else None
         p.keep_states = 1 if keep_states else 0
-        p.flags = QT_FLAG_TIME_KERNELS if time_kernels else 0
+        p.flags = (QT_FLAG_TIME_KERNELS if time_kernels else 0) | (QT_FLAG_MULTI_GATE if grouping else 0)
         p.stream = stream
         self.params = p
         self.num_traj = num_traj

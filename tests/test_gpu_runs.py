@@ -114,6 +114,22 @@ def test_grid_depolarizing_tf32x3(qt, orc, k):
     assert run.stats()["flushes"] == 0
 
 
+def test_multi_gate_passes_match_single_gate_passes(qt, orc):
+    """Grouping fused gates into multi-gate passes changes only the pass count:
+    same branch records, same states within float rounding, fewer passes."""
+    circ = qs.config1_circuit(rows=4, cols=5, depth=12, gamma=1e-2, lam=1e-2)
+    f = qt.Fused(qt.Circuit.from_synth(circ), 4)
+    a = qt.Run(f, 4, seed=2, keep_states=True, grouping=True)
+    b = qt.Run(f, 4, seed=2, keep_states=True, grouping=False)
+    np.testing.assert_array_equal(a.kraus_indices()[0], b.kraus_indices()[0])
+    for t in range(4):
+        assert rel_l2(a.state(t), b.state(t)) < 2e-6
+    sa, sb = a.stats(), b.stats()
+    assert sa["fused_pieces"] == sb["fused_pieces"]
+    assert sa["fused_passes"] < sb["fused_passes"]
+    compare_run(qt, orc, circ, 4, k=4, mode=qt.QT_DELAYED, seed=2, S=100)
+
+
 def test_mixture_only_circuit_never_flushes(qt, orc):
     circ = qs.config3_circuit(rows=2, cols=5, depth=10, p=0.05)
     run, _ = compare_run(qt, orc, circ, 8, k=4, mode=qt.QT_DELAYED, S=50)
