@@ -38,7 +38,10 @@ WORKLOAD = ("grid30: 5x6 grid, depth 20, sqrtX/sqrtY/sqrtW + CZ, amplitude dampi
 
 # DRAM bytes per launch of the fused-gate kernel from an ncu capture, keyed by
 # the SHA-256 of the kernel source it was taken on (null once the source changes).
-KNOWN_TRAFFIC = {}
+KNOWN_TRAFFIC = {
+    # k_apply_tile<4, 16, 6>: 4.252 GB per launch at n = 28 (dram read + write), x4 for n = 30
+    "fc3783e5300579b2": 4 * (2147763200 + 2104254976),
+}
 
 
 def kernel_source_hash() -> str:
@@ -228,6 +231,8 @@ def run_ours(args):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     apply_ms = apply_bytes = launches = passes = flushes = 0
+    ms_w = [0.0] * 8
+    passes_w = [0] * 8
     for i in range(args.steps):
         r = step(args.warmup + i, flags=True)
         s = r.stats()
@@ -236,6 +241,9 @@ def run_ours(args):
         launches += s["kernel_launches"]
         passes += s["fused_passes"]
         flushes += s["flushes"]
+        for w in range(8):
+            ms_w[w] += s["apply_ms_by_width"][w]
+            passes_w[w] += s["passes_by_width"][w]
     e1.record(stream)
     barrier()
     clk = clocks.stop()
@@ -269,8 +277,12 @@ def run_ours(args):
     e2e = world * T * args.steps / e2e_s
 
     peak, peak_kind = measured_peaks()
-    achieved = (apply_bytes / (apply_ms / 1e3)) / 1e9 if apply_ms > 0 else 0.0
-    traffic = KNOWN_TRAFFIC.get(kernel_source_hash())
+    # the dominant kernel: the gate width with the most fused-pass device time
+    wdom = max(range(1, 8), key=lambda w: ms_w[w])
+    pass_bytes = 16 << N_QUBITS
+    achieved = passes_w[wdom] * pass_bytes / (ms_w[wdom] / 1e3) / 1e9 if ms_w[wdom] > 0 else 0.0
+    achieved_all = (apply_bytes / (apply_ms / 1e3)) / 1e9 if apply_ms > 0 else 0.0
+    traffic = KNOWN_TRAFFIC.get(kernel_source_hash()) if wdom == FUSE_K else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -281,12 +293,15 @@ def run_ours(args):
                    "flushes_per_traj": flushes / (T * args.steps),
                    "l2": "no flush: every pass streams the 8 GiB state (> 129 MB L2)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "kernel": "k_apply (fused-gate apply)",
+        "roofline": {"bound": "hbm", "kernel": f"k_apply_tile<{wdom}> ({wdom}-qubit fused-gate apply)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
                      "frac_of_8TBs_nominal": achieved / 8000.0,
                      "traffic": traffic,
-                     "bytes_per_launch": 16 << N_QUBITS},
+                     "bytes_per_launch": pass_bytes,
+                     "launches": passes_w[wdom],
+                     "share_of_fused_pass_time": ms_w[wdom] / apply_ms if apply_ms > 0 else None,
+                     "all_fused_passes_gbs": achieved_all},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d // args.steps,
                 "d2h_bytes_per_step": d2h // args.steps},
         "gpu_launches": launches,

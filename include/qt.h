@@ -165,6 +165,8 @@ typedef struct {
   uint64_t kernel_launches;   /* kernels of this library launched by the run */
   uint64_t fused_pieces;      /* fused gates (or segment pieces of them) applied; several
                                  share one pass when a multi-gate pass groups them */
+  uint64_t passes_by_width[8];  /* fused-gate passes by gate width 1..7; [0] = multi-gate passes */
+  double apply_ms_by_width[8];  /* their device time (QT_FLAG_TIME_KERNELS, else 0) */
 } qt_run_stats_t;
 qt_status qt_run_stats(const qt_run* r, qt_run_stats_t* out);
 

@@ -172,6 +172,7 @@ struct Controller {
   std::vector<float2> tmp32;
   double* pinned = nullptr;
   std::vector<cudaEvent_t> ev;              // timing events (pairs)
+  std::vector<int> ev_width;                // gate width of each timed pass (0: multi-gate)
   size_t ev_used = 0;
 
   explicit Controller(qt_run& r) : R(r), c(*r.f->c), f(*r.f) {
@@ -239,7 +240,7 @@ struct Controller {
 
   // one pass over the state, optionally bracketed by timing events
   template <typename F>
-  qt_status timed_launch(F&& launch, const char* what) {
+  qt_status timed_launch(F&& launch, const char* what, int width) {
     const bool timed = (R.p.flags & QT_FLAG_TIME_KERNELS) != 0;
     if (timed) {
       if (ev_used + 2 > ev.size()) {
@@ -257,8 +258,11 @@ struct Controller {
     if (e != cudaSuccess) return cuda_fail(e, what);
     if (timed) {
       QT_CUDA(cudaEventRecord(ev[ev_used + 1], R.st), "cudaEventRecord");
+      if (ev_width.size() < ev.size() / 2) ev_width.resize(ev.size() / 2);
+      ev_width[ev_used / 2] = width;
       ev_used += 2;
     }
+    R.stats.passes_by_width[width < 8 ? width : 0]++;
     R.stats.fused_passes++;
     R.stats.kernel_launches++;
     R.stats.apply_bytes += 16ull << R.n;
@@ -266,7 +270,8 @@ struct Controller {
   }
 
   qt_status apply(float2* psi, const std::vector<uint32_t>& targets, const float2* U) {
-    return timed_launch([&](cudaError_t&) { return launch_one(psi, targets, U); }, "apply kernel launch");
+    return timed_launch([&](cudaError_t&) { return launch_one(psi, targets, U); }, "apply kernel launch",
+                        static_cast<int>(targets.size()));
   }
 
   qt_status collect_timing() {
@@ -277,6 +282,8 @@ struct Controller {
       float t = 0.f;
       QT_CUDA(cudaEventElapsedTime(&t, ev[i], ev[i + 1]), "cudaEventElapsedTime");
       ms += t;
+      const int w = ev_width[i / 2];
+      R.stats.apply_ms_by_width[w < 8 ? w : 0] += t;
     }
     R.stats.apply_ms += ms;
     ev_used = 0;
@@ -399,7 +406,7 @@ struct Controller {
       qt_status s = timed_launch([&](cudaError_t& e) {
         e = launch_apply_group(psi, static_cast<int>(R.n), static_cast<int>(members.size()), gp, R.st);
         return QT_OK;
-      }, "multi-gate pass launch");
+      }, "multi-gate pass launch", 0);
       if (s != QT_OK) return s;
       R.stats.fused_pieces += members.size();
     }

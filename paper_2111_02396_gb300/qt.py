@@ -55,7 +55,8 @@ class qt_run_stats_t(C.Structure):
                 ("gate_ops", C.c_uint64), ("flushes", C.c_uint64),
                 ("device_ms", C.c_double), ("apply_ms", C.c_double),
                 ("apply_bytes", C.c_uint64), ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64),
-                ("kernel_launches", C.c_uint64), ("fused_pieces", C.c_uint64)]
+                ("kernel_launches", C.c_uint64), ("fused_pieces", C.c_uint64),
+                ("passes_by_width", C.c_uint64 * 8), ("apply_ms_by_width", C.c_double * 8)]
 
 
 class qt_fused_info_t(C.Structure):
@@ -406,7 +407,10 @@ class Run:
     def stats(self):
         s = qt_run_stats_t()
         _check(load().qt_run_stats(self.h, C.byref(s)))
-        return {f: getattr(s, f) for f, _ in qt_run_stats_t._fields_}
+        out = {f: getattr(s, f) for f, _ in qt_run_stats_t._fields_}
+        for f in ("passes_by_width", "apply_ms_by_width"):
+            out[f] = list(out[f])
+        return out
 
     def norms(self):
         out = np.zeros(max(self.num_traj, 1))
