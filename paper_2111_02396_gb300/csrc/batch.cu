@@ -9,8 +9,9 @@
 //   - one CTA per SM takes trajectories from an atomic counter, largest
 //     state first;
 //   - a state of up to 2^14 amplitudes lives in the CTA's shared memory;
-//     larger states live in a per-CTA slot of global memory (L2-resident
-//     for the sizes of this form);
+//     larger states live in a per-CTA slot of global memory (up to 2^18
+//     amplitudes, 304 MB over 152 CTAs, so they stream from DRAM, and each
+//     thread keeps 16 amplitude loads in flight to cover the latency);
 //   - stage 1 of Alg. 2 for every channel is decided on the device with the
 //     same Philox4x32-10 draws as the plain loop; stage-2 flush points cut
 //     the circuit into segments exactly as in the plain loop, and within a
@@ -118,22 +119,36 @@ __device__ void cta_apply_w(float2* psi, int n, const int* order, const float2* 
       if ((m >> b) & 1) o |= 1ull << order[b];
     off[m] = o;
   }
+  // B sets per thread per round, all of their 16 amplitudes loaded before
+  // any arithmetic: a state in global memory needs that many loads in
+  // flight per thread to cover the memory latency
+  constexpr int B = D >= 16 ? 1 : 16 / D;
   const uint64_t sets = 1ull << (n - W);
-  for (uint64_t s = threadIdx.x; s < sets; s += blockDim.x) {
-    const uint64_t base = insert_zeros(s, W, sorted);
-    float2 v[D];
+  const uint64_t stride = static_cast<uint64_t>(blockDim.x);
+  for (uint64_t s0 = threadIdx.x; s0 < sets; s0 += B * stride) {
+    uint64_t base[B];
+    float2 v[B][D];
 #pragma unroll
-    for (int m = 0; m < D; ++m) v[m] = psi[base | off[m]];
+    for (int b = 0; b < B; ++b) {
+      const uint64_t s = s0 + b * stride;
+      base[b] = insert_zeros(s < sets ? s : s0, W, sorted);
 #pragma unroll
-    for (int j = 0; j < D; ++j) {
-      float xr = 0.f, xi = 0.f;
+      for (int m = 0; m < D; ++m) v[b][m] = psi[base[b] | off[m]];
+    }
 #pragma unroll
-      for (int m = 0; m < D; ++m) {
-        const float2 a = A[j * D + m];
-        xr = fmaf(a.x, v[m].x, fmaf(-a.y, v[m].y, xr));
-        xi = fmaf(a.x, v[m].y, fmaf(a.y, v[m].x, xi));
+    for (int b = 0; b < B; ++b) {
+      if (s0 + b * stride >= sets) break;
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        float xr = 0.f, xi = 0.f;
+#pragma unroll
+        for (int m = 0; m < D; ++m) {
+          const float2 a = A[j * D + m];
+          xr = fmaf(a.x, v[b][m].x, fmaf(-a.y, v[b][m].y, xr));
+          xi = fmaf(a.x, v[b][m].y, fmaf(a.y, v[b][m].x, xi));
+        }
+        psi[base[b] | off[j]] = make_float2(xr, xi);
       }
-      psi[base | off[j]] = make_float2(xr, xi);
     }
   }
 }

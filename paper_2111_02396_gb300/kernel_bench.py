@@ -44,9 +44,16 @@ def main(argv=None):
                     help="instead: time whole trajectories of the damped grid workload on a ROWS x COLS grid")
     ap.add_argument("--fuse", type=int, default=4, help="--grid: fusion width")
     ap.add_argument("--grouping", action="store_true", help="--grid: multi-gate passes")
+    ap.add_argument("--batch", type=int, metavar="COUNT",
+                    help="time the batched persistent kernel on COUNT circuits of the mixed-width workload")
+    ap.add_argument("--threads", type=int, default=512, help="--batch: threads per CTA")
+    ap.add_argument("--min-n", type=int, default=0, help="--batch: keep circuits with n >= this")
+    ap.add_argument("--max-n", type=int, default=64, help="--batch: keep circuits with n <= this")
     args = ap.parse_args(argv)
     if args.grid:
         return grid_runs(args)
+    if args.batch:
+        return batch_runs(args)
     pkg.load()
     n = args.n
     st = torch.cuda.current_stream()
@@ -88,6 +95,38 @@ def main(argv=None):
         print(json.dumps(dict(kernel="expect16", n=n, ms=ms, gbs=gbs)), flush=True)
         ms, gbs = timeit(lambda: pkg.qt_state_sample(d.data_ptr(), n, 0, 0, 100, stream=st.cuda_stream), 8 << n)
         print(json.dumps(dict(kernel="sample100", n=n, ms=ms, gbs=gbs)), flush=True)
+
+
+def batch_runs(args):
+    """The batched persistent form on circuits of the 8192-circuit workload (n ~ U{8..18})."""
+    import torch
+
+    import paper_2111_02396_gb300 as pkg
+    import qtsynth as qs
+    pkg.load()
+    ccs, i = [], 0
+    while len(ccs) < args.batch:
+        cc = qs.config2_compact(i)
+        if args.min_n <= cc.num_qubits <= args.max_n:
+            ccs.append(cc)
+        i += 1
+    fused = pkg.fuse_many([pkg.Circuit.from_compact(c) for c in ccs], args.fuse)
+    b = pkg.Batch(fused)
+    sh = torch.cuda.current_stream().cuda_stream
+    for w in range(args.warmup):
+        b.run(seed=0, first_traj=w * args.batch, samples_per_traj=100, threads=args.threads, stream=sh)
+    ms = []
+    for r in range(args.reps):
+        b.run(seed=0, first_traj=(args.warmup + r) * args.batch, samples_per_traj=100, threads=args.threads,
+              stream=sh)
+        ms.append(b.stats()["device_ms"])
+    amps = np.array([1 << c.num_qubits for c in ccs], dtype=np.float64)
+    nf = np.array([f.info()["num_fused"] for f in fused], dtype=np.float64)
+    med = float(np.median(ms))
+    row = dict(kernel="batch", count=args.batch, fuse=args.fuse, threads=args.threads, min_n=args.min_n,
+               max_n=args.max_n, ms=med, traj_per_s=args.batch / (med / 1e3),
+               eff_gbs=float(np.sum(nf * amps * 16)) / (med / 1e3) / 1e9)
+    print(json.dumps(row), flush=True)
 
 
 def grid_runs(args):

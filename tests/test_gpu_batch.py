@@ -5,7 +5,7 @@ the FP64 oracle run of the same circuit, seed and trajectory id (branch
 records where the margin exceeds 1e-6, final state within relative L2
 2e-5 / fidelity 1 - 1e-5, samples where the CDF margin exceeds 1e-6), and
 with the plain per-trajectory loop.  Covers states in shared memory
-(n <= 14) and in global memory (n = 15, 16), forced stage-2 flushes, CUDA
+(n <= 14) and in global memory (n = 15..18), forced stage-2 flushes, CUDA
 graph replay, and the autotuner.
 """
 import numpy as np
@@ -82,6 +82,15 @@ def test_batch_workload_circuits_match_oracle(qt, orc):
 def test_batch_forced_flushes(qt, orc, k):
     ccs = [_noisy(n, 10, s, 0.06) for s, n in enumerate([8, 9, 10, 11, 12, 15])]
     b, _ = check_batch(qt, orc, ccs, k, seed=3, first=100, S=64, threads=256)
+    assert b.stats()["flushes"] > 0
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_batch_global_memory_states_match_oracle(qt, orc, k):
+    """States of 2^15..2^18 amplitudes (a CTA's slot of global memory, 16 loads in flight per
+    thread) next to shared-memory states, with forced stage-2 flushes."""
+    ccs = [_noisy(n, 6, s, 0.08) for s, n in enumerate([15, 16, 17, 18, 9, 12])]
+    b, _ = check_batch(qt, orc, ccs, k, seed=5, first=300, S=64, threads=512)
     assert b.stats()["flushes"] > 0
 
 
