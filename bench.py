@@ -399,7 +399,8 @@ def run_batch(args):
         "form": "batched",
         "config": {"workload": BATCH_WORKLOAD, "trajectories_per_step": num, "fuse_k": best_k,
                    "threads_per_cta": best_t, "cuda_graph": True,
-                   "l2": "states live in shared memory / L2; inputs resident"},
+                   "l2": "states of <= 2^14 amplitudes in shared memory, larger ones in per-CTA global "
+                         "slots (304 MB at n = 18, streamed from DRAM); inputs resident"},
         "plain_loop": {"value": plain, "unit": UNIT,
                        "sample": f"every {stride}th circuit ({len(idx)} trajectories), qt_run_trajectories "
                                  f"one trajectory at a time on the same GPU, scaled by {stride}"},
