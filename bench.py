@@ -186,6 +186,40 @@ def run_reference(args):
 # ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
+def delayed_vs_eager(pkg, fused, sh, traj0, T=2):
+    """The same trajectories (seed 0, ids traj0..) with delayed and with eager inner products
+    (Alg. 2 vs the conventional per-channel evaluation): device time per trajectory, and the
+    number of branch records that differ (the two-stage partition makes both modes pick the
+    same operator for the same draw; a difference can only come from a draw within rounding
+    of a boundary)."""
+    d = pkg.Run(fused, T, seed=0, first_traj=traj0, mode=pkg.QT_DELAYED, stream=sh)
+    e = pkg.Run(fused, T, seed=0, first_traj=traj0, mode=pkg.QT_EAGER, stream=sh)
+    kd, ke = d.kraus_indices()[0], e.kraus_indices()[0]
+    sd, se = d.stats(), e.stats()
+    return {"trajectories": T, "delayed_ms_per_traj": sd["device_ms"] / T,
+            "eager_ms_per_traj": se["device_ms"] / T,
+            "eager_over_delayed": se["device_ms"] / sd["device_ms"],
+            "probability_passes_per_traj": {"delayed": sd["prob_passes"] / T, "eager": se["prob_passes"] / T},
+            "branch_records": int(kd.size), "differing_branch_records": int((kd != ke).sum())}
+
+
+def bandwidth_probe(pkg, qs, sh):
+    """One noiseless trajectory of the 32-qubit 4x8 grid (32 GiB state), depth 20, fused to k = 4:
+    the fused-gate passes' rate per gate width, timed with events around every pass."""
+    circ = qs.grid_circuit(4, 8, 20, 0)
+    f = pkg.Fused(pkg.Circuit.from_synth(circ), FUSE_K)
+    r = pkg.Run(f, 1, seed=0, time_kernels=True, stream=sh)
+    st = r.stats()
+    by_w = {}
+    for w in range(1, 8):
+        if st["passes_by_width"][w]:
+            by_w[str(w)] = {"passes": st["passes_by_width"][w],
+                            "gbs": st["passes_by_width"][w] * (16 << 32) / (st["apply_ms_by_width"][w] / 1e3) / 1e9}
+    return {"workload": "noiseless 4x8 grid (n = 32, 32 GiB complex64), depth 20, fused k = 4, one trajectory",
+            "ms": st["device_ms"], "fused_passes": st["fused_passes"],
+            "all_passes_gbs": st["apply_bytes"] / (st["apply_ms"] / 1e3) / 1e9, "by_width": by_w}
+
+
 def run_ours(args):
     import torch
 
@@ -307,6 +341,10 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk,
     }
+    line["amplitude_updates_per_s"] = world * passes * float(1 << N_QUBITS) / (ms / 1e3)
+    if rank == 0 and not args.no_extras:
+        line["delayed_vs_eager"] = delayed_vs_eager(pkg, fused, sh, base + 9_000_000)
+        line["bandwidth_probe_n32"] = bandwidth_probe(pkg, qs, sh)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, desc, _ = oracle_sample(target_s=args.ref_seconds)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
@@ -348,7 +386,7 @@ def run_batch(args):
     stream = torch.cuda.Stream()
     sh = stream.cuda_stream
     t0 = time.perf_counter()
-    best_k, best_t, table = pkg.autotune_batch(qcs, sample=256, kmin=2, kmax=4, stream=sh)
+    best_k, best_t, table = pkg.autotune_batch(qcs, sample=256, kmin=2, kmax=6, stream=sh)
     t_tune = time.perf_counter() - t0
     t0 = time.perf_counter()
     fused = pkg.fuse_many(qcs, best_k)
@@ -391,6 +429,7 @@ def run_batch(args):
     nf = np.array([f.info()["num_fused"] for f in fused], dtype=np.float64)
     eff_bytes = float(np.sum(nf * amps * 16))
     eff_gbs = eff_bytes / (statistics.median(ms) / 1e3) / 1e9
+    amp_updates = float(np.sum(nf * amps)) / (statistics.median(ms) / 1e3)
     peak, peak_kind = measured_peaks()
     line = {
         "metric": METRIC, "value": batched, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
@@ -405,6 +444,7 @@ def run_batch(args):
                        "sample": f"every {stride}th circuit ({len(idx)} trajectories), qt_run_trajectories "
                                  f"one trajectory at a time on the same GPU, scaled by {stride}"},
         "speedup_vs_plain": batched / plain,
+        "amplitude_updates_per_s": amp_updates,
         "effective_bandwidth": {"achieved": eff_gbs, "peak": peak, "unit": "GB/s", "frac": eff_gbs / peak,
                                 "peak_kind": peak_kind,
                                 "note": "algorithmic bytes (16 B x 2^n per fused pass) / kernel time; "
@@ -550,9 +590,10 @@ def run_precision(args):
     # throughput and norm drift at n = 32
     c32 = qs.config3_circuit()
     f32 = pkg.Fused(pkg.Circuit.from_synth(c32), 6)
-    T = args.traj_precision
     res = {}
     for name, prec in (("tf32x3", pkg.QT_TF32X3), ("fp32", pkg.QT_FP32)):
+        # the 32 trajectories of the workload on tensor cores; the slower FP32 comparator on a few
+        T = args.traj_precision if prec == pkg.QT_TF32X3 else min(args.traj_precision, 4)
         pkg.Run(f32, 1, seed=0, first_traj=10_000, precision=prec, stream=sh)     # warm-up
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -561,13 +602,15 @@ def run_precision(args):
         torch.cuda.synchronize()
         st = r.stats()
         ms = e0.elapsed_time(e1)
-        res[name] = {"traj_per_s": T / (ms / 1e3), "apply_gbs": st["apply_bytes"] / (st["apply_ms"] / 1e3) / 1e9,
+        res[name] = {"trajectories": T, "traj_per_s": T / (ms / 1e3),
+                     "amplitude_updates_per_s": st["fused_passes"] * float(1 << 32) / (ms / 1e3),
+                     "apply_gbs": st["apply_bytes"] / (st["apply_ms"] / 1e3) / 1e9,
                      "fused_passes_per_traj": st["fused_passes"] / T,
                      "norm_drift_max": float(np.max(np.abs(r.norms() - 1.0)))}
     out["n32"] = res
     out["value"] = res["tf32x3"]["traj_per_s"]
     out["steps"], out["warmup"] = 1, 1
-    out["ms_per_step"] = 1e3 * T / res["tf32x3"]["traj_per_s"]
+    out["ms_per_step"] = 1e3 * res["tf32x3"]["trajectories"] / res["tf32x3"]["traj_per_s"]
     peak, kind = measured_peaks()
     out["roofline"] = {"bound": "hbm", "kernel": "k_apply_tc<6> (split-TF32 tcgen05)",
                        "achieved": res["tf32x3"]["apply_gbs"], "peak": peak, "unit": "GB/s",
@@ -680,13 +723,15 @@ def main():
     ap.add_argument("--traj", type=int, default=16, help="trajectories per step per GPU")
     ap.add_argument("--ref-seconds", type=float, default=15.0, help="oracle sample length")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="grid30: skip the delayed-vs-eager comparison and the 32-qubit bandwidth probe")
     ap.add_argument("--workload", choices=["grid30", "chain10", "batch", "serve", "precision", "noise-sweep"],
                     default="grid30",
                     help="grid30: the plain loop at scale (default); batch: the batched form; "
                          "serve: the serving loop")
     ap.add_argument("--requests", type=int, default=120, help="serve: requests of the stream")
     ap.add_argument("--slots", type=int, default=8, help="serve: concurrent requests")
-    ap.add_argument("--traj-precision", type=int, default=2, help="precision: trajectories at n=32")
+    ap.add_argument("--traj-precision", type=int, default=32, help="precision: trajectories at n=32")
     ap.add_argument("--batch-size", type=int, default=8192)
     ap.add_argument("--plain-stride", type=int, default=32)
     args = ap.parse_args()

@@ -272,7 +272,7 @@ typedef struct {
 qt_status qt_batch_stats(const qt_batch* b, qt_batch_stats_t* out);
 void qt_batch_destroy(qt_batch* b);
 /* Autotuner of the batched form: on a spread sample of `sample` circuits
- * (0 = 256) it fuses at every width kmin..kmax (<= 4), times the batched
+ * (0 = 256) it fuses at every width kmin..kmax (<= 6), times the batched
  * kernel (warm-up + 2 timed runs) at 128, 256 and 512 threads per CTA, and
  * returns the fastest width and CTA size.  table (optional) receives the
  * mean ms per run, [(k - kmin) * 3 + {128, 256, 512}]. */

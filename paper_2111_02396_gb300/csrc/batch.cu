@@ -42,7 +42,7 @@
 namespace qt {
 namespace bt {
 
-constexpr int kMaxW = 4;            // widest fused gate in the batched form
+constexpr int kMaxW = 6;            // widest fused gate in the batched form
 constexpr int kSmemNMax = 14;       // states up to 2^14 amplitudes in shared memory
 constexpr int kMaxN = 20;           // widest state of the batched form
 
@@ -62,7 +62,7 @@ struct Set {
 };
 struct Gate {
   uint8_t w, t[kMaxW];
-  uint8_t pad[3];
+  uint8_t pad[1];
   uint32_t mat, mem0, nmem, minpos, maxpos;
 };
 struct Dev {
@@ -99,7 +99,7 @@ __device__ __forceinline__ uint64_t insert_zeros(uint64_t x, int w, const int* s
 }
 
 // psi <- A psi on qubits order[0..W) (basis bit b <-> order[b]); A (row-major) in smem
-template <int W>
+template <int W, bool GLOBAL>
 __device__ void cta_apply_w(float2* psi, int n, const int* order, const float2* A) {
   constexpr int D = 1 << W;
   int sorted[W];
@@ -121,8 +121,9 @@ __device__ void cta_apply_w(float2* psi, int n, const int* order, const float2* 
   }
   // B sets per thread per round, all of their 16 amplitudes loaded before
   // any arithmetic: a state in global memory needs that many loads in
-  // flight per thread to cover the memory latency
-  constexpr int B = D >= 16 ? 1 : 16 / D;
+  // flight per thread to cover the memory latency (a shared-memory state
+  // does not, and there the extra registers cost more than they save)
+  constexpr int B = (!GLOBAL || D >= 16) ? 1 : 16 / D;
   const uint64_t sets = 1ull << (n - W);
   const uint64_t stride = static_cast<uint64_t>(blockDim.x);
   for (uint64_t s0 = threadIdx.x; s0 < sets; s0 += B * stride) {
@@ -153,6 +154,42 @@ __device__ void cta_apply_w(float2* psi, int n, const int* order, const float2* 
   }
 }
 
+// widths 5 and 6: one gather set per thread, its 2^w members in a local
+// array (registers or, at w = 6, local memory); kept out of line so that its
+// register demand does not raise that of the rest of the kernel
+template <int W>
+__device__ __noinline__ void cta_apply_wide(float2* psi, int n, const int* order, const float2* A) {
+  constexpr int D = 1 << W;
+  int sorted[W];
+  for (int b = 0; b < W; ++b) sorted[b] = order[b];
+  for (int i = 1; i < W; ++i)
+    for (int j = i; j > 0; --j)
+      if (sorted[j - 1] > sorted[j]) { const int t = sorted[j]; sorted[j] = sorted[j - 1]; sorted[j - 1] = t; }
+  const uint64_t sets = 1ull << (n - W);
+  for (uint64_t s = threadIdx.x; s < sets; s += blockDim.x) {
+    const uint64_t base = insert_zeros(s, W, sorted);
+    float2 v[D];
+    for (int m = 0; m < D; ++m) {
+      uint64_t o = 0;
+      for (int b = 0; b < W; ++b)
+        if ((m >> b) & 1) o |= 1ull << order[b];
+      v[m] = psi[base | o];
+    }
+    for (int j = 0; j < D; ++j) {
+      float xr = 0.f, xi = 0.f;
+      for (int m = 0; m < D; ++m) {
+        const float2 a = A[j * D + m];
+        xr = fmaf(a.x, v[m].x, fmaf(-a.y, v[m].y, xr));
+        xi = fmaf(a.x, v[m].y, fmaf(a.y, v[m].x, xi));
+      }
+      uint64_t o = 0;
+      for (int b = 0; b < W; ++b)
+        if ((j >> b) & 1) o |= 1ull << order[b];
+      psi[base | o] = make_float2(xr, xi);
+    }
+  }
+}
+
 __device__ void cta_apply(float2* psi, int n, int w, const int* order, const float2* Aglob, float scale,
                           float2* smat) {
   const int D = 1 << w;
@@ -163,10 +200,12 @@ __device__ void cta_apply(float2* psi, int n, int w, const int* order, const flo
   }
   __syncthreads();
   switch (w) {
-    case 1: cta_apply_w<1>(psi, n, order, smat); break;
-    case 2: cta_apply_w<2>(psi, n, order, smat); break;
-    case 3: cta_apply_w<3>(psi, n, order, smat); break;
-    default: cta_apply_w<4>(psi, n, order, smat); break;
+    case 1: n > kSmemNMax ? cta_apply_w<1, true>(psi, n, order, smat) : cta_apply_w<1, false>(psi, n, order, smat); break;
+    case 2: n > kSmemNMax ? cta_apply_w<2, true>(psi, n, order, smat) : cta_apply_w<2, false>(psi, n, order, smat); break;
+    case 3: n > kSmemNMax ? cta_apply_w<3, true>(psi, n, order, smat) : cta_apply_w<3, false>(psi, n, order, smat); break;
+    case 4: n > kSmemNMax ? cta_apply_w<4, true>(psi, n, order, smat) : cta_apply_w<4, false>(psi, n, order, smat); break;
+    case 5: cta_apply_wide<5>(psi, n, order, smat); break;
+    default: cta_apply_wide<6>(psi, n, order, smat); break;
   }
 }
 
@@ -297,7 +336,7 @@ __device__ __forceinline__ int decide_stage1(const Set& st, const double* pbar, 
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(512) k_batch(const __grid_constant__ Dev d) {
   extern __shared__ __align__(16) float2 s_state[];
-  __shared__ float2 s_mat[256];
+  float2* s_mat = s_state + (1u << kSmemNMax);   // the pass's matrix, up to 64 x 64
   __shared__ double s_red[32][17];
   __shared__ double s_rho[16];
   __shared__ double s_wcum[32];
@@ -810,7 +849,7 @@ qt_status qt_batch_run(qt_batch* b, const qt_batch_params* p) {
   }
   b->hrun[0] = p->seed;
   b->hrun[1] = p->first_traj;
-  const size_t smem = sizeof(float2) << bt::kSmemNMax;
+  const size_t smem = (sizeof(float2) << bt::kSmemNMax) + sizeof(float2) * (1u << (2 * bt::kMaxW));
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [&] {

@@ -78,7 +78,7 @@ def test_batch_workload_circuits_match_oracle(qt, orc):
     check_batch(qt, orc, ccs, 3)
 
 
-@pytest.mark.parametrize("k", [2, 4])
+@pytest.mark.parametrize("k", [2, 4, 5, 6])
 def test_batch_forced_flushes(qt, orc, k):
     ccs = [_noisy(n, 10, s, 0.06) for s, n in enumerate([8, 9, 10, 11, 12, 15])]
     b, _ = check_batch(qt, orc, ccs, k, seed=3, first=100, S=64, threads=256)
@@ -127,7 +127,8 @@ def test_batch_graph_replay(qt):
 def test_batch_autotuner(qt):
     ccs = _workload_circuits(max_n=18, count=48)
     qcs = [qt.Circuit.from_compact(c) for c in ccs]
-    k, threads, table = qt.autotune_batch(qcs, sample=24, kmin=2, kmax=4)
-    assert k in (2, 3, 4) and threads in (128, 256, 512)
+    k, threads, table = qt.autotune_batch(qcs, sample=24, kmin=2, kmax=6)
+    assert k in (2, 3, 4, 5, 6) and threads in (128, 256, 512)
+    assert len(table) == 15
     assert all(v > 0 for v in table.values())
     assert table[(k, threads)] == min(table.values())
