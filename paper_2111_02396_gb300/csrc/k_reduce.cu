@@ -220,9 +220,115 @@ __global__ void __launch_bounds__(kRedThreads) k_expect(const float2* __restrict
   block_reduce_store<W>(acc, partial);
 }
 
+// n >= 9: a warp takes blocks of 512 amplitudes and lane l holds the 16
+// amplitudes x = (blk << 9) | (j << 6) | (l << 1) | e, j = 0..7, e = 0..1,
+// read with eight coalesced 128-bit loads.  Over the bits that vary inside
+// the thread (0, 6, 7, 8) its 16 weights are Walsh-Hadamard transformed,
+//   W[u] = sum_v (-1)^popc(u & v) w[v],   v = e | (j << 1),
+// so that the block's share of sum_x |psi_x|^2 (-1)^popc(x & m) is
+// (-1)^(parity of m on the fixed bits) * W[u_m], u_m being m's bits 0, 6, 7,
+// 8.  The parity over the lane bits (1..5) is fixed per thread and the one
+// over the block bits (>= 9) is one popc, so a mask costs a few instructions
+// per 16 amplitudes.  FP32 runs cover 8 blocks (128 amplitudes per thread),
+// then FP64.
+struct ExpWArgs {
+  uint32_t mblk[kExpGroup];     // mask bits >= 9, shifted down by 9
+  uint32_t mlane[kExpGroup];    // mask bits 1..5, shifted down by 1
+  uint32_t u[kExpGroup];        // mask bits (0, 6, 7, 8) as a 4-bit index
+  int nm;
+  uint64_t num_blocks;          // 2^(n - 9)
+};
+
+constexpr int kExpWChunk = 8;
+
+__global__ void __launch_bounds__(kRedThreads) k_expect_wht(const float2* __restrict__ psi,
+                                                            const __grid_constant__ ExpWArgs a,
+                                                            double* __restrict__ partial) {
+  constexpr int W = kExpGroup + 1;
+  __shared__ float s_w[kRedThreads][17];        // each thread's transformed weights (padded row)
+  double acc[W];
+  float f[W];
+#pragma unroll
+  for (int c = 0; c < W; ++c) { acc[c] = 0.0; f[c] = 0.f; }
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+  uint32_t slane = 0;                           // bit m: parity of mask m on the lane bits
+  for (int m = 0; m < a.nm; ++m) slane |= (static_cast<uint32_t>(__popc(lane & a.mlane[m])) & 1u) << m;
+  const float4* p4 = reinterpret_cast<const float4*>(psi);
+  float* row = s_w[threadIdx.x];
+  int cnt = 0;
+  for (uint64_t blk = warp; blk < a.num_blocks; blk += nwarps) {
+    float w[16];
+    float4 q[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) q[j] = __ldg(p4 + (blk << 8) + j * 32 + lane);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      w[2 * j] = fmaf(q[j].x, q[j].x, q[j].y * q[j].y);
+      w[2 * j + 1] = fmaf(q[j].z, q[j].z, q[j].w * q[j].w);
+    }
+    if (a.nm > 0) {
+#pragma unroll
+      for (int h = 1; h < 16; h <<= 1)
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          if ((i & h) == 0) {
+            const float x = w[i], y = w[i | h];
+            w[i] = x + y;
+            w[i | h] = x - y;
+          }
+      f[0] += w[0];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) row[u] = w[u];
+      const uint32_t b32 = static_cast<uint32_t>(blk);
+#pragma unroll
+      for (int m = 0; m < kExpGroup; ++m) {
+        if (m < a.nm) {
+          const float val = row[a.u[m]];
+          const uint32_t sgn = (static_cast<uint32_t>(__popc(b32 & a.mblk[m])) ^ (slane >> m)) & 1u;
+          f[1 + m] += sgn ? -val : val;
+        }
+      }
+    } else {
+      float t = 0.f;
+#pragma unroll
+      for (int v = 0; v < 16; ++v) t += w[v];
+      f[0] += t;
+    }
+    if (++cnt == kExpWChunk) {
+#pragma unroll
+      for (int k = 0; k < W; ++k) { acc[k] += static_cast<double>(f[k]); f[k] = 0.f; }
+      cnt = 0;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < W; ++k) acc[k] += static_cast<double>(f[k]);
+  block_reduce_store<W>(acc, partial);
+}
+
 cudaError_t launch_expect(const float2* psi, int n, int nm, const uint64_t* masks,
                           const Scratch& scr, cudaStream_t st) {
   if (nm > kExpGroup || n < 1) return cudaErrorInvalidValue;
+  if (n >= 9) {
+    ExpWArgs a;
+    for (int m = 0; m < kExpGroup; ++m) {
+      const uint64_t mk = m < nm ? masks[m] : 0;
+      a.mblk[m] = static_cast<uint32_t>(mk >> 9);
+      a.mlane[m] = static_cast<uint32_t>((mk >> 1) & 31u);
+      a.u[m] = static_cast<uint32_t>((mk & 1u) | (((mk >> 6) & 7u) << 1));
+    }
+    a.nm = nm;
+    a.num_blocks = 1ull << (n - 9);
+    static int gridw = 0;
+    static std::once_flag oncew;
+    std::call_once(oncew, [] { gridw = red_grid(k_expect_wht, ~0ull >> 1); });
+    const uint64_t need = (a.num_blocks * 32 + kRedThreads - 1) / kRedThreads;
+    const int g = static_cast<int>(need < static_cast<uint64_t>(gridw) ? need : gridw);
+    k_expect_wht<<<g, kRedThreads, 0, st>>>(psi, a, scr.partial);
+    k_finalize<<<1, 64, 0, st>>>(scr.partial, g, kExpGroup + 1, scr.result);
+    return cudaGetLastError();
+  }
   ExpArgs a;
   for (int m = 0; m < kExpGroup; ++m) a.masks[m] = m < nm ? masks[m] : 0;
   a.nm = nm;

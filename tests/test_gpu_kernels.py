@@ -134,12 +134,12 @@ def test_probabilities_from_reduced_density(qt, orc, n, q):
         assert abs(np.trace(rho).real - orc.norm2(psi.astype(np.complex128))) < 1e-6
 
 
-@pytest.mark.parametrize("n", [1, 6, 15, 22])
+@pytest.mark.parametrize("n", [1, 6, 8, 9, 10, 15, 22])
 def test_expect_z(qt, orc, n):
     psi = random_state(n, 7) * np.float32(1.3)
     d = to_device(psi)
     rng = np.random.default_rng(n)
-    masks = [1 << j for j in range(n)] + [int(x) for x in rng.integers(0, 1 << n, 20)]
+    masks = [0, (1 << n) - 1] + [1 << j for j in range(n)] + [int(x) for x in rng.integers(0, 1 << n, 20)]
     got = qt.qt_state_expect_z(d.data_ptr(), n, masks)
     want = orc.expect_z(psi.astype(np.complex128), masks)
     np.testing.assert_allclose(got, want, atol=2e-6)
