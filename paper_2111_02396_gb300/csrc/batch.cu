@@ -857,10 +857,17 @@ qt_status qt_batch_run(qt_batch* b, const qt_batch_params* p) {
   });
   if (attr != cudaSuccess) return set_error(QT_ERR_CUDA, "qt_batch_run: smem attribute: %s", cudaGetErrorString(attr));
   const unsigned grid = static_cast<unsigned>(std::min<uint64_t>(sm_count(), b->num));
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  cudaError_t e = cudaSuccess;
+  struct Events {                   // the run's timing events, destroyed on every return
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~Events() {
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+    }
+  } ev;
+  cudaError_t e = cudaEventCreate(&ev.a);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev.b);
+  if (e != cudaSuccess) return set_error(QT_ERR_CUDA, "qt_batch_run: cudaEventCreate: %s", cudaGetErrorString(e));
+  cudaEvent_t e0 = ev.a, e1 = ev.b;
   auto enqueue = [&](cudaStream_t s) -> cudaError_t {
     cudaError_t r = cudaMemcpyAsync(static_cast<uint8_t*>(b->counter.p) + 16, b->hrun, 2 * sizeof(uint64_t),
                                     cudaMemcpyHostToDevice, s);
@@ -870,8 +877,8 @@ qt_status qt_batch_run(qt_batch* b, const qt_batch_params* p) {
     bt::k_batch<<<grid, threads, smem, s>>>(d);
     return cudaGetLastError();
   };
-  cudaEventRecord(e0, st);
-  if (p->use_graph && st) {
+  e = cudaEventRecord(e0, st);
+  if (e == cudaSuccess && p->use_graph && st) {
     // the graph copies the run parameters from pinned memory when it runs, so
     // it is rebuilt only when the launch shape changes
     if (b->gexec && b->g_threads != threads) {
@@ -889,10 +896,10 @@ qt_status qt_batch_run(qt_batch* b, const qt_batch_params* p) {
       b->g_threads = threads;
     }
     if (e == cudaSuccess) e = cudaGraphLaunch(b->gexec, st);
-  } else {
+  } else if (e == cudaSuccess) {
     e = enqueue(st);
   }
-  cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
   b->last = *p;
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->kraus.data(), d.kraus, sizeof(int32_t) * b->total_ch, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->stage.data(), d.stage, sizeof(int32_t) * b->total_ch, cudaMemcpyDeviceToHost, st);
@@ -901,9 +908,7 @@ qt_status qt_batch_run(qt_batch* b, const qt_batch_params* p) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->flushes.data(), d.flushes, sizeof(uint32_t) * b->num, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   float ms = 0.f;
-  if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
   if (e != cudaSuccess) return set_error(QT_ERR_CUDA, "qt_batch_run: %s", cudaGetErrorString(e));
   b->device_ms = ms;
   return QT_OK;
