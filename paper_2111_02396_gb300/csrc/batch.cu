@@ -49,6 +49,7 @@ constexpr int kMaxN = 20;           // widest state of the batched form
 struct Traj {
   uint32_t n, gate0, ngates, op0, nops, ch0, nch, chop0;   // ch0: output offset; chop0: ch_op table offset
   uint64_t arena_off;               // amplitude offset of the kept state (keep_states)
+  uint32_t gf0, pad;                // offset of this trajectory's per-gate flags (per trajectory, like ch0)
 };
 struct Op {
   uint8_t kind, q, q0, q1;
@@ -79,6 +80,7 @@ struct Dev {
   uint64_t slot_amps;               // amplitudes per CTA slot (0: use traj.arena_off)
   int32_t* kraus;
   int32_t* stage;
+  uint8_t* gflag;                   // per fused gate of the run: a member channel holds a non-default stage-1 choice
   uint64_t* samples;
   uint32_t* flushes;
   unsigned int* counter;
@@ -373,6 +375,20 @@ __global__ void __launch_bounds__(512) k_batch(const __grid_constant__ Dev d) {
     }
     if (tid == 0) { s_pend_pos = -1; s_pend_choice = 0; s_scale = 1.f; }
     __syncthreads();
+    // which fused gates cannot use their precomputed matrix because a member
+    // channel took a non-default stage-1 choice (or none): decided once per
+    // trajectory, one gate per thread, so that the pass loop below reads one
+    // flag per gate instead of chasing each member's tables
+    for (uint32_t g = tid; g < T.ngates; g += blockDim.x) {
+      const Gate G = d.gates[T.gate0 + g];
+      uint8_t fl = 0;
+      for (uint32_t mi = 0; mi < G.nmem && !fl; ++mi) {
+        const Op op = d.ops[T.op0 + d.members[G.mem0 + mi]];
+        if (op.channel >= 0 && d.kraus[T.ch0 + op.channel] != static_cast<int>(d.sets[op.set].def)) fl = 1;
+      }
+      d.gflag[T.gf0 + g] = fl;
+    }
+    __syncthreads();
     uint32_t lo = 0, cur_ch = 0, nflush = 0;
     for (;;) {
       // next flush point
@@ -391,15 +407,13 @@ __global__ void __launch_bounds__(512) k_batch(const __grid_constant__ Dev d) {
       for (uint32_t g = 0; g < T.ngates; ++g) {
         const Gate G = d.gates[T.gate0 + g];
         if (G.maxpos < lo || G.minpos >= hi) continue;
-        bool dflt = G.minpos >= lo && G.maxpos < hi;
-        for (uint32_t mi = 0; dflt && mi < G.nmem; ++mi) {
-          const uint32_t pos = d.members[G.mem0 + mi];
-          const Op op = d.ops[T.op0 + pos];
-          if (op.channel >= 0) {
-            if (static_cast<int>(pos) == pend_pos) dflt = false;
-            else if (d.kraus[T.ch0 + op.channel] != static_cast<int>(d.sets[op.set].def)) dflt = false;
-          }
-        }
+        bool dflt = G.minpos >= lo && G.maxpos < hi && !d.gflag[T.gf0 + g];
+        // the channel decided in stage 2 at this segment's start is applied as
+        // its normalized Kraus operator, so the gate holding it is never default
+        if (dflt && pend_pos >= 0 && static_cast<uint32_t>(pend_pos) >= G.minpos &&
+            static_cast<uint32_t>(pend_pos) <= G.maxpos)
+          for (uint32_t mi = 0; dflt && mi < G.nmem; ++mi)
+            if (static_cast<int>(d.members[G.mem0 + mi]) == pend_pos) dflt = false;
         if (dflt) {
           int order[kMaxW];
           for (int b = 0; b < G.w; ++b) order[b] = G.t[b];
@@ -560,7 +574,8 @@ struct qt_batch {
   DevMem tables, arena, outs, counter;
   uint64_t* hrun = nullptr;         // pinned {seed, first_traj}; the graph copies it to counter+16
   bt::Dev dev{};
-  size_t off_kraus = 0, off_stage = 0, off_samples = 0, off_flushes = 0, off_err = 0;
+  size_t off_kraus = 0, off_stage = 0, off_samples = 0, off_flushes = 0, off_err = 0, off_gflag = 0;
+  uint64_t total_gates = 0;         // sum of the trajectories' fused-gate counts (one flag each per run)
   uint32_t S = 0, keep = 0;
   qt_batch_params last{};
   // results on the host
@@ -651,8 +666,10 @@ qt_status qt_batch_create(uint32_t num, const qt_fused* const* fused, qt_batch**
       const bt::Traj& P = B->traj[seen->second];
       bt::Traj& T = B->traj[i];
       T = P;
-      T.ch0 = B->total_ch;                 // outputs are per trajectory
+      T.ch0 = B->total_ch;                 // outputs and per-run flags are per trajectory
       B->total_ch += T.nch;
+      T.gf0 = static_cast<uint32_t>(B->total_gates);
+      B->total_gates += T.ngates;
       B->gate_ops += f->gate_ops;
       continue;
     }
@@ -670,6 +687,8 @@ qt_status qt_batch_create(uint32_t num, const qt_fused* const* fused, qt_batch**
     T.nch = static_cast<uint32_t>(c.channel_op.size());
     T.gate0 = static_cast<uint32_t>(gates.size());
     T.ngates = static_cast<uint32_t>(f->gates.size());
+    T.gf0 = static_cast<uint32_t>(B->total_gates);
+    B->total_gates += T.ngates;
     B->total_ch += T.nch;
     B->max_n = std::max(B->max_n, c.n);
     std::vector<uint32_t> local_sets;   // set ids by op
@@ -826,12 +845,14 @@ qt_status qt_batch_run(qt_batch* b, const qt_batch_params* p) {
     b->off_stage = off; off = align(off + sizeof(int32_t) * std::max<uint32_t>(b->total_ch, 1));
     b->off_samples = off; off = align(off + sizeof(uint64_t) * std::max<uint64_t>(uint64_t(b->num) * b->S, 1));
     b->off_flushes = off; off = align(off + sizeof(uint32_t) * b->num);
+    b->off_gflag = off; off = align(off + std::max<uint64_t>(b->total_gates, 1));
     if (!b->outs.alloc(off)) return set_error(QT_ERR_OUT_OF_MEMORY, "qt_batch_run: outputs");
     uint8_t* o = static_cast<uint8_t*>(b->outs.p);
     d.kraus = reinterpret_cast<int32_t*>(o + b->off_kraus);
     d.stage = reinterpret_cast<int32_t*>(o + b->off_stage);
     d.samples = reinterpret_cast<uint64_t*>(o + b->off_samples);
     d.flushes = reinterpret_cast<uint32_t*>(o + b->off_flushes);
+    d.gflag = o + b->off_gflag;
     int sms = sm_count();
     const uint64_t slot = b->max_n > static_cast<uint32_t>(bt::kSmemNMax) ? (1ull << b->max_n) : 0;
     const uint64_t arena_amps = b->keep ? b->total_amps : slot * sms;
