@@ -12,6 +12,6 @@ vectors); no function is "parity unpinned".
 """
 from .oracle import (  # noqa: F401
     build, lib_path, philox4x32_10, u01, apply, norm2, kraus_norms, lower_bound,
-    run_trajectory, run_trajectories, sample, expect_z, density_evolve,
+    run_trajectory, run_trajectories, sample, readout, expect_z, density_evolve,
     DELAYED, EAGER, CUMULATIVE, FlatCircuit,
 )

@@ -14,6 +14,7 @@
  *                       algorithm it is compared with (Sec. III.E)
  *   orc_sample          bitstring measurement of all qubits (Sec. V.C)
  *   orc_expect_z        Z-string expectations (densities, Sec. V.C)
+ *   orc_readout         readout bit flips of sampled bitstrings (Sec. V.A)
  *   orc_density_evolve  exact channel evolution rho -> sum_i K_i rho K_i^dag
  */
 #include "oracle.h"
@@ -420,6 +421,21 @@ void orc_sample(const orc_cplx* psi, int n, uint64_t seed, uint64_t traj, int S,
   }
   free(t);
   free(order);
+}
+
+/* Readout errors (Sec. V.A): a qubit in |b> is reported as the other value
+ * with the error probability measured for b (p00 error for b = 0, p11 error
+ * for b = 1).  One draw per qubit per sample, on its own Philox stream. */
+void orc_readout(uint64_t* bits, int S, int n, const double* err, uint64_t seed, uint64_t traj) {
+  for (int j = 0; j < S; j++) {
+    uint64_t x = bits[j];
+    for (int q = 0; q < n; q++) {
+      const int b = (int)((x >> q) & 1u);
+      const double u = orc_u01(seed, traj, 2, ((uint32_t)j << 6) | (uint32_t)q);
+      if (u < err[2 * q + b]) x ^= (uint64_t)1 << q;
+    }
+    bits[j] = x;
+  }
 }
 
 void orc_expect_z(const orc_cplx* psi, int n, int M, const uint64_t* masks, double* out) {

@@ -82,6 +82,13 @@ void orc_sample(const orc_cplx* psi, int n, uint64_t seed, uint64_t traj, int S,
 /* <Z_mask> = sum_x |psi_x|^2 (-1)^popcount(x & mask) / <psi|psi>. */
 void orc_expect_z(const orc_cplx* psi, int n, int M, const uint64_t* masks, double* out);
 
+/* Readout errors (Sec. V.A, parallel readout errors): qubit q of sample j,
+ * whose true value is b, is read as 1 - b with probability err[2q + b]
+ * (err[2q] = P(read 1 | 0), err[2q + 1] = P(read 0 | 1)).  The decision
+ * draws u = u01 from Philox stream 2 at index (j << 6) | q and flips when
+ * u < err[2q + b].  bits[0..S) is modified in place. */
+void orc_readout(uint64_t* bits, int S, int n, const double* err, uint64_t seed, uint64_t traj);
+
 /* Exact density-matrix evolution of the whole circuit from |0..0><0..0|:
  * rho <- U rho U^dag for gates, rho <- sum_i K_i rho K_i^dag for channels.
  * rho is 4^n complex, element (r, c) at index r + c * 2^n. */

@@ -69,6 +69,7 @@ def _load():
                                                  C.c_int, P, P, P, P, P]
             lib.orc_sample.argtypes = [P, C.c_int, C.c_uint64, C.c_uint64, C.c_int, P, P]
             lib.orc_expect_z.argtypes = [P, C.c_int, C.c_int, P, P]
+            lib.orc_readout.argtypes = [P, C.c_int, C.c_int, P, C.c_uint64, C.c_uint64]
             lib.orc_density_evolve.argtypes = [P, P]
             _lib = lib
     return _lib
@@ -205,6 +206,17 @@ def sample(psi, seed, traj, S):
     mg = np.zeros(max(S, 1), dtype=np.float64)
     lib.orc_sample(_ptr(psi), n, seed, traj, S, _ptr(out), _ptr(mg))
     return out[:S], mg[:S]
+
+
+def readout(bits, n, err, seed, traj):
+    """Readout errors (Sec. V.A) applied to sampled bitstrings: err is [n, 2] with
+    err[q] = (P(read 1 | 0), P(read 0 | 1)).  Returns a new array."""
+    lib = _load()
+    out = np.ascontiguousarray(np.array(bits, dtype=np.uint64, copy=True))
+    e = np.ascontiguousarray(np.asarray(err, dtype=np.float64).reshape(n, 2))
+    if out.size:
+        lib.orc_readout(_ptr(out), int(out.size), n, _ptr(e), seed, traj)
+    return out
 
 
 def expect_z(psi, masks):
