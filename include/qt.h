@@ -113,6 +113,12 @@ typedef struct {
                                   QT_FLAG_MULTI_GATE: several fused gates per pass */
   void* stream;                /* cudaStream_t (0 = legacy default stream) */
   uint64_t timeout_ns;         /* bound on any device wait (0 = 10 s) */
+  const double* readout_error; /* NULL, or readout errors of the samples (Sec. V.A, parallel
+                                  readout errors), 2 per qubit, copied: qubit q of true value b is
+                                  reported as 1 - b with probability readout_error[2q + b]
+                                  (the p00 error for b = 0, the p11 error for b = 1), decided
+                                  by u01(seed, traj, 2, (j << 6) | q) < readout_error[2q + b]
+                                  for sample j; needs samples_per_traj < 2^26 */
 } qt_run_params;
 
 /* Run num_traj trajectories of Alg. 2 (QT_DELAYED) or of the conventional
@@ -219,9 +225,10 @@ qt_status qt_state_apply(void* state, uint32_t n, uint32_t q, const uint32_t* qu
  * 4^q complex, row-major.  P_i = tr(K_i^dag K_i rho) (Alg. 2 step 14). */
 qt_status qt_state_reduced_density(const void* state, uint32_t n, uint32_t q,
                                    const uint32_t* qubits, double* out, void* stream);
-/* S bitstrings from |psi|^2 with uniforms u01(seed, traj, 1, j); out host. */
+/* S bitstrings from |psi|^2 with uniforms u01(seed, traj, 1, j); out host.
+ * readout_error: NULL, or 2 per qubit as in qt_run_params (host, copied). */
 qt_status qt_state_sample(const void* state, uint32_t n, uint64_t seed, uint64_t traj,
-                          uint32_t S, uint64_t* out, void* stream);
+                          uint32_t S, uint64_t* out, const double* readout_error, void* stream);
 /* Z-string expectations of the state (normalized by <psi|psi>); out host. */
 qt_status qt_state_expect_z(const void* state, uint32_t n, uint32_t num_terms,
                             const uint64_t* z_masks, double* out, void* stream);

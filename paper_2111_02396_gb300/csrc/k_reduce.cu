@@ -442,9 +442,13 @@ __global__ void __launch_bounds__(1024) k_cdf_scan(double* __restrict__ cum, uin
   for (uint64_t i = lo; i < hi; ++i) { r += cum[i]; cum[i] = r; }
 }
 
+// ro (optional): readout errors (Sec. V.A), 2 per qubit: qubit q of value b
+// is reported as 1 - b when u01(seed, traj, 2, (j << 6) | q) < ro[2q + b];
+// lane l decides qubits l and l + 32, and the flips are OR-combined.
 __global__ void k_sample(const float2* __restrict__ psi, uint64_t namps, const float* __restrict__ sub,
                          uint64_t nsub, const double* __restrict__ cum, uint64_t nblk, uint64_t seed,
-                         uint64_t traj, uint32_t S, uint64_t* __restrict__ out) {
+                         uint64_t traj, uint32_t S, uint64_t* __restrict__ out, int n,
+                         const double* __restrict__ ro) {
   const int lane = threadIdx.x & 31;
   const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
@@ -503,12 +507,23 @@ __global__ void k_sample(const float2* __restrict__ psi, uint64_t namps, const f
       run += tot;
     }
     if (x == ~0ull) x = last_nz;     // rounding put t past the sub-block end
+    if (ro) {
+      unsigned long long flips = 0ull;
+      for (int q = lane; q < n; q += 32) {
+        const uint32_t b = static_cast<uint32_t>((x >> q) & 1ull);
+        const double u = uniform01(seed, traj, kStreamReadout, (static_cast<uint32_t>(j) << 6) | static_cast<uint32_t>(q));
+        if (u < ro[2 * q + b]) flips |= 1ull << q;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) flips |= __shfl_xor_sync(0xffffffffu, flips, o);
+      x ^= flips;
+    }
     if (lane == 0) out[j] = x;
   }
 }
 
 cudaError_t launch_sample(const float2* psi, int n, uint64_t seed, uint64_t traj, uint32_t S,
-                          uint64_t* out, const Scratch& scr, cudaStream_t st) {
+                          uint64_t* out, const Scratch& scr, cudaStream_t st, const double* readout) {
   if (n < 1) return cudaErrorInvalidValue;
   const uint64_t namps = 1ull << n;
   const uint64_t nsub = cdf_num_sub(n), nblk = cdf_num_blk(n);
@@ -525,7 +540,7 @@ cudaError_t launch_sample(const float2* psi, int n, uint64_t seed, uint64_t traj
     uint64_t gs = (S + wpb - 1) / wpb;
     if (gs > cap) gs = cap;
     k_sample<<<static_cast<unsigned>(gs), threads, 0, st>>>(psi, namps, scr.cdf_sub, nsub, scr.cdf_cum,
-                                                           nblk, seed, traj, S, out);
+                                                           nblk, seed, traj, S, out, n, readout);
   }
   return cudaGetLastError();
 }

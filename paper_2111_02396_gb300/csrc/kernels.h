@@ -39,7 +39,7 @@ cudaError_t launch_expect(const float2* psi, int n, int nm, const uint64_t* mask
                           const Scratch& scr, cudaStream_t st);
 // S samples of trajectory traj into out (device)
 cudaError_t launch_sample(const float2* psi, int n, uint64_t seed, uint64_t traj, uint32_t S,
-                          uint64_t* out, const Scratch& scr, cudaStream_t st);
+                          uint64_t* out, const Scratch& scr, cudaStream_t st, const double* readout = nullptr);
 // 6-qubit fused gate on CUDA cores (FP32), matrix 64x64 row-major in device memory, n >= 13
 cudaError_t launch_apply6_fp32(float2* psi, int n, const uint32_t* targets, const float2* udev, cudaStream_t st);
 // multi-gate pass: up to kGroupMaxGates fused gates (width <= 4, targets

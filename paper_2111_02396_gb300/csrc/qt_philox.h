@@ -48,6 +48,6 @@ QT_HD double uniform01(uint64_t seed, uint64_t traj, uint32_t stream, uint32_t i
   return static_cast<double>(bits) * 0x1.0p-53;
 }
 
-enum : uint32_t { kStreamChannel = 0, kStreamSample = 1 };
+enum : uint32_t { kStreamChannel = 0, kStreamSample = 1, kStreamReadout = 2 };
 
 }  // namespace qt

@@ -133,6 +133,7 @@ struct qt_run {
   std::vector<uint64_t> samples;
   std::vector<double> expect, norms;
   std::vector<DevBuf> states;
+  DevBuf readout;                  // 2n readout error probabilities (device), or empty
   ScratchBufs scr;
   qt_run_stats_t stats{};
   cudaStream_t st = nullptr;
@@ -513,7 +514,8 @@ struct Controller {
     R.norms[t] = N;
     if (R.p.samples_per_traj) {
       QT_CUDA(launch_sample(psi, static_cast<int>(R.n), R.p.seed, traj, R.p.samples_per_traj,
-                            d_samples + static_cast<size_t>(t) * R.p.samples_per_traj, R.scr.s, R.st),
+                            d_samples + static_cast<size_t>(t) * R.p.samples_per_traj, R.scr.s, R.st,
+                            R.readout.as<const double>()),
               "sampling kernel launch");
       R.stats.kernel_launches += 4;
     }
@@ -536,6 +538,17 @@ qt_status qt_set_allocator(qt_alloc_fn alloc, qt_free_fn free_fn, void* ctx) {
   return QT_OK;
 }
 
+// readout errors: 2n probabilities in [0, 1]; the sample index must fit the
+// Philox counter layout (j << 6) | q
+static qt_status check_readout(const double* ro, uint32_t n, uint64_t S, const char* who) {
+  if (!ro) return QT_OK;
+  if (S >= (1ull << 26)) return set_error(QT_ERR_INVALID_ARG, "%s: readout errors need fewer than 2^26 samples", who);
+  for (uint32_t i = 0; i < 2 * n; ++i)
+    if (!(ro[i] >= 0.0 && ro[i] <= 1.0))
+      return set_error(QT_ERR_INVALID_ARG, "%s: readout error %u is %g (must be in [0, 1])", who, i, ro[i]);
+  return QT_OK;
+}
+
 qt_status qt_run_trajectories(const qt_fused* f, const qt_run_params* p, qt_run** out) {
   clear_error();
   if (!f || !p || !out) return set_error(QT_ERR_INVALID_ARG, "qt_run_trajectories: NULL argument");
@@ -548,6 +561,10 @@ qt_status qt_run_trajectories(const qt_fused* f, const qt_run_params* p, qt_run*
     return set_error(QT_ERR_INVALID_ARG, "qt_run_trajectories: z_masks is NULL");
   const Circuit& c = *f->c;
   if (c.n < 1) return set_error(QT_ERR_INVALID_ARG, "qt_run_trajectories: empty circuit");
+  {
+    const qt_status rs = check_readout(p->readout_error, c.n, p->samples_per_traj, "qt_run_trajectories");
+    if (rs != QT_OK) return rs;
+  }
   for (const auto& g : f->gates)
     if (g.targets.size() > 5 && c.n < 13)
       return set_error(QT_ERR_UNSUPPORTED, "qt_run_trajectories: fused width %zu needs n >= 13", g.targets.size());
@@ -556,6 +573,7 @@ qt_status qt_run_trajectories(const qt_fused* f, const qt_run_params* p, qt_run*
   R->f = f;
   R->p = *p;
   R->p.z_masks = nullptr;
+  R->p.readout_error = nullptr;
   R->masks.assign(p->z_masks, p->z_masks + p->num_z_masks);
   R->n = c.n;
   R->T = p->num_traj;
@@ -570,6 +588,13 @@ qt_status qt_run_trajectories(const qt_fused* f, const qt_run_params* p, qt_run*
   R->stats.num_channels = R->nch;
   if (!R->scr.alloc(static_cast<int>(c.n), R->st))
     return set_error(QT_ERR_OUT_OF_MEMORY, "qt_run_trajectories: scratch allocation");
+  if (p->readout_error) {
+    if (!R->readout.alloc(sizeof(double) * 2 * c.n, R->st))
+      return set_error(QT_ERR_OUT_OF_MEMORY, "qt_run_trajectories: readout errors");
+    QT_CUDA(cudaMemcpyAsync(R->readout.p, p->readout_error, sizeof(double) * 2 * c.n, cudaMemcpyHostToDevice, R->st),
+            "cudaMemcpyAsync(readout)");
+    R->stats.h2d_bytes += sizeof(double) * 2 * c.n;
+  }
   const size_t sbytes = sizeof(float2) << c.n;
   DevBuf work, dsamp;
   if (!p->keep_states && !work.alloc(sbytes, R->st))
@@ -650,7 +675,7 @@ qt_status qt_sample(qt_run* r, uint32_t S, uint64_t* out) {
   if (!d.alloc(sizeof(uint64_t) * S * r->T, r->st)) return set_error(QT_ERR_OUT_OF_MEMORY, "qt_sample: buffer");
   for (uint32_t t = 0; t < r->T; ++t)
     QT_CUDA(launch_sample(r->states[t].as<float2>(), static_cast<int>(r->n), r->p.seed, r->p.first_traj + t, S,
-                          d.as<uint64_t>() + static_cast<size_t>(t) * S, r->scr.s, r->st),
+                          d.as<uint64_t>() + static_cast<size_t>(t) * S, r->scr.s, r->st, r->readout.as<const double>()),
             "sampling kernel launch");
   QT_CUDA(cudaMemcpyAsync(out, d.p, sizeof(uint64_t) * S * r->T, cudaMemcpyDeviceToHost, r->st), "cudaMemcpyAsync");
   QT_CUDA(cudaStreamSynchronize(r->st), "cudaStreamSynchronize");
@@ -818,17 +843,24 @@ qt_status qt_state_reduced_density(const void* state, uint32_t n, uint32_t q, co
 }
 
 qt_status qt_state_sample(const void* state, uint32_t n, uint64_t seed, uint64_t traj, uint32_t S, uint64_t* out,
-                          void* stream) {
+                          const double* readout_error, void* stream) {
   clear_error();
   qt_status s = check_state(state, n, "qt_state_sample");
   if (s != QT_OK) return s;
   if (S && !out) return set_error(QT_ERR_INVALID_ARG, "qt_state_sample: out is NULL");
+  s = check_readout(readout_error, n, S, "qt_state_sample");
+  if (s != QT_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   ScratchBufs scr;
-  DevBuf d;
-  if (!scr.alloc(static_cast<int>(n), st) || (S && !d.alloc(sizeof(uint64_t) * S, st)))
+  DevBuf d, ro;
+  if (!scr.alloc(static_cast<int>(n), st) || (S && !d.alloc(sizeof(uint64_t) * S, st)) ||
+      (readout_error && !ro.alloc(sizeof(double) * 2 * n, st)))
     return set_error(QT_ERR_OUT_OF_MEMORY, "qt_state_sample: scratch");
-  QT_CUDA(launch_sample(static_cast<const float2*>(state), static_cast<int>(n), seed, traj, S, d.as<uint64_t>(), scr.s, st),
+  if (readout_error)
+    QT_CUDA(cudaMemcpyAsync(ro.p, readout_error, sizeof(double) * 2 * n, cudaMemcpyHostToDevice, st),
+            "cudaMemcpyAsync(readout)");
+  QT_CUDA(launch_sample(static_cast<const float2*>(state), static_cast<int>(n), seed, traj, S, d.as<uint64_t>(), scr.s, st,
+                        ro.as<const double>()),
           "qt_state_sample");
   if (S) QT_CUDA(cudaMemcpyAsync(out, d.p, sizeof(uint64_t) * S, cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
   QT_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");

@@ -46,7 +46,8 @@ class qt_run_params(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("first_traj", C.c_uint64), ("num_traj", C.c_uint32),
                 ("mode", C.c_uint32), ("precision", C.c_uint32), ("samples_per_traj", C.c_uint32),
                 ("num_z_masks", C.c_uint32), ("z_masks", C.c_void_p), ("keep_states", C.c_uint32),
-                ("flags", C.c_uint32), ("stream", C.c_void_p), ("timeout_ns", C.c_uint64)]
+                ("flags", C.c_uint32), ("stream", C.c_void_p), ("timeout_ns", C.c_uint64),
+                ("readout_error", C.c_void_p)]
 
 
 class qt_run_stats_t(C.Structure):
@@ -164,7 +165,7 @@ def load(build_if_missing: bool = True):
             "qt_channel_lower_bounds": [P, u32, P, C.c_size_t, P],
             "qt_state_apply": [P, u32, u32, P, P, u32, P],
             "qt_state_reduced_density": [P, u32, u32, P, P, P],
-            "qt_state_sample": [P, u32, u64, u64, u32, P, P],
+            "qt_state_sample": [P, u32, u64, u64, u32, P, P, P],
             "qt_state_expect_z": [P, u32, u32, P, P, P],
             "qt_state_reduced_density_noalloc": [P, u32, u32, P, P, P],
             "qt_fuse_many": [u32, P, u32, u32, P],
@@ -366,10 +367,15 @@ class Fused:
 class Run:
     def __init__(self, fused: Fused, num_traj, *, seed=0, first_traj=0, mode=QT_DELAYED,
                  precision=QT_FP32, samples_per_traj=0, z_masks=(), keep_states=False,
-                 time_kernels=False, grouping=False, stream=None):
+                 time_kernels=False, grouping=False, readout_error=None, stream=None):
+        """readout_error: None, or [n, 2] readout error probabilities per qubit,
+        (P(read 1 | 0), P(read 0 | 1)), applied to the samples (Sec. V.A)."""
         lib = load()
         self.fused = fused
         self.masks = np.ascontiguousarray(np.asarray(z_masks, dtype=np.uint64))
+        n = fused.circuit.num_qubits
+        self._ro = (None if readout_error is None else
+                    np.ascontiguousarray(np.asarray(readout_error, np.float64).reshape(n, 2)))
         p = qt_run_params()
         p.seed, p.first_traj, p.num_traj = seed, first_traj, num_traj
         p.mode, p.precision, p.samples_per_traj = mode, precision, samples_per_traj
@@ -378,6 +384,7 @@ class Run:
         p.keep_states = 1 if keep_states else 0
         p.flags = (QT_FLAG_TIME_KERNELS if time_kernels else 0) | (QT_FLAG_MULTI_GATE if grouping else 0)
         p.stream = stream
+        p.readout_error = self._ro.ctypes.data if self._ro is not None else None
         self.params = p
         self.num_traj = num_traj
         self.S = samples_per_traj
@@ -446,9 +453,12 @@ def qt_state_reduced_density(state_ptr, n, qubits, stream=None):
     return out.reshape(D, D)
 
 
-def qt_state_sample(state_ptr, n, seed, traj, S, stream=None):
+def qt_state_sample(state_ptr, n, seed, traj, S, readout_error=None, stream=None):
+    """readout_error: None, or [n, 2] probabilities (P(read 1 | 0), P(read 0 | 1)) per qubit."""
     out = np.zeros(max(S, 1), dtype=np.uint64)
-    _check(load().qt_state_sample(state_ptr, n, seed, traj, S, _ptr(out), stream))
+    ro = None if readout_error is None else np.ascontiguousarray(np.asarray(readout_error, np.float64).reshape(n, 2))
+    _check(load().qt_state_sample(state_ptr, n, seed, traj, S, _ptr(out), _ptr(ro) if ro is not None else None,
+                                  stream))
     return out[:S]
 
 

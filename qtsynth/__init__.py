@@ -13,7 +13,7 @@ from .circuits import (  # noqa: F401
     fsim, random_unitary,
     chain_circuit, grid_circuit, config0_circuit, config1_circuit,
     config2_circuit, config3_circuit, serving_requests,
-    ghz_circuit, qft_circuit, random_noisy_circuit,
+    ghz_circuit, qft_circuit, random_noisy_circuit, noise_model_circuit,
 )
 from .circuits import request_circuit  # noqa: F401,E402
 from .compact import CompactCircuit, layered_compact, config2_compact, request_compact  # noqa: F401,E402

@@ -348,6 +348,81 @@ def request_circuit(req):
 # --------------------------------------------------------------------------
 # small closed-form circuits and random test circuits
 # --------------------------------------------------------------------------
+def noise_model_circuit(rows, cols, depth, seed, *, t1q=25e-9, t2q=32e-9, T1=20e-6, Tphi=30e-6,
+                        sigma_theta=0.01, sigma_phi=0.02, sigma_z=0.01, p1=1e-3, p2=5e-3,
+                        p00=0.01, p11=0.04):
+    """The approximate hardware noise model of Sec. V.B on a rows x cols grid,
+    with synthetic parameters (no calibration data is used).
+
+    Each layer: one gate per qubit from {sqrtX, sqrtY, sqrtW} (no repeat),
+    followed on each qubit by the decay + dephasing channel for the gate
+    duration t1q and by 1q depolarizing p1; then fSim(pi/2, pi/6) on the
+    layer's grid couplings, each with Z phase errors exp(i a Z) before and
+    after on both qubits, the coherent error fSim(dtheta, dphi) after it,
+    the decay + dephasing channel for t2q on both qubits, and 2q
+    depolarizing p2 (the D = 4 Pauli mixture).  The coherent error angles
+    are drawn once per coupling (normal, sigma_theta / sigma_phi), the Z
+    phases once per coupling and qubit (normal, sigma_z).
+
+    Returns (circuit, readout) with readout [n, 2] = (p00 error, p11 error)
+    per qubit, drawn around p00 and p11 (the p11 error is the larger, as
+    the paper expects from decay during measurement)."""
+    n = rows * cols
+    rng = np.random.default_rng([0x57, rows, cols, depth, seed])
+    c = Circuit(n, name=f"noise_model{rows}x{cols}x{depth}")
+    coh = {}
+    prev = None
+    m = 0
+
+    def rz(a):
+        return np.diag([np.exp(1j * a), np.exp(-1j * a)]).astype(np.complex128)
+
+    for layer in range(depth):
+        choice = _one_qubit_layer(rng, n, prev)
+        prev = choice
+        for q in range(n):
+            c.gate(GATE_SET[choice[q]], (q,), m)
+        m += 1
+        for q in range(n):
+            c.channel(decay_dephasing(t1q, T1, Tphi), (q,), m)
+        m += 1
+        for q in range(n):
+            c.channel(depolarizing(p1), (q,), m)
+        m += 1
+        pairs = _grid_couplings(rows, cols, n, layer)
+        for (a, b) in pairs:
+            if (a, b) not in coh:
+                coh[(a, b)] = (rng.normal(0.0, sigma_theta), rng.normal(0.0, sigma_phi),
+                               rng.normal(0.0, sigma_z, 4))
+        for (a, b) in pairs:
+            z = coh[(a, b)][2]
+            c.gate(rz(z[0]), (a,), m)
+            c.gate(rz(z[1]), (b,), m)
+        m += 1
+        for (a, b) in pairs:
+            c.gate(fsim(np.pi / 2, np.pi / 6), (a, b), m)
+        m += 1
+        for (a, b) in pairs:
+            dth, dph, _ = coh[(a, b)]
+            c.gate(fsim(dth, dph), (a, b), m)
+        m += 1
+        for (a, b) in pairs:
+            z = coh[(a, b)][2]
+            c.gate(rz(z[2]), (a,), m)
+            c.gate(rz(z[3]), (b,), m)
+        m += 1
+        touched = sorted({q for p in pairs for q in p})
+        for q in touched:
+            c.channel(decay_dephasing(t2q, T1, Tphi), (q,), m)
+        m += 1
+        for (a, b) in pairs:
+            c.channel(depolarizing(p2, 2), (a, b), m)
+        m += 1
+    readout = np.stack([np.clip(rng.normal(p00, p00 / 4, n), 0.0, 1.0),
+                        np.clip(rng.normal(p11, p11 / 4, n), 0.0, 1.0)], axis=1)
+    return c, readout
+
+
 def ghz_circuit(n):
     c = Circuit(n, name=f"ghz{n}")
     c.gate(H, (0,), 0)

@@ -57,6 +57,15 @@ def _circ(n, ops):
     return c
 
 
+def test_readout_errors_are_validated(qt):
+    from paper_2111_02396_gb300.qt import QtError, QT_ERR_INVALID_ARG
+    f = qt.Fused(qt.Circuit.from_synth(qs.config0_circuit()), 2)
+    for bad in (np.full((10, 2), 1.5), np.full((10, 2), -0.1), np.full((10, 2), np.nan)):
+        with pytest.raises(QtError) as ei:
+            qt.Run(f, 1, samples_per_traj=4, readout_error=bad)
+        assert ei.value.status == QT_ERR_INVALID_ARG
+
+
 def test_validation_errors(qt):
     from paper_2111_02396_gb300.qt import QtError, QT_ERR_INVALID_ARG, QT_ERR_NOT_CPTP
     good = qs.Op(qs.KIND_GATE, (0,), qs.SQRT_X[None], None, 0)

@@ -162,6 +162,29 @@ def test_sample_parity(qt, orc, n, S):
         assert np.all(np.abs(got[~ok].astype(np.int64) - want[~ok].astype(np.int64)) <= 64)
 
 
+@pytest.mark.parametrize("n,S", [(1, 200), (11, 3000), (33, 64)])
+def test_sample_readout_errors(qt, orc, n, S):
+    """Readout errors (Sec. V.A) on the device sampler: the same flips as the oracle's
+    readout of the oracle's samples, wherever the sample itself is not a tie."""
+    rng = np.random.default_rng(n + 5)
+    ro = np.stack([rng.uniform(0, 0.3, n), rng.uniform(0, 0.5, n)], axis=1)
+    if n <= 20:
+        psi = random_state(n, 13)
+        d = to_device(psi)
+        want, margin = orc.sample(psi.astype(np.complex128), 8, 2, S)
+    else:                                        # 2^33 amplitudes: the all-zero basis state
+        torch = torch_cuda()
+        d = torch.zeros(1 << n, dtype=torch.complex64, device="cuda")
+        d[0] = 1.0
+        want, margin = np.zeros(S, dtype=np.uint64), np.ones(S)
+    got = qt.qt_state_sample(d.data_ptr(), n, 8, 2, S, readout_error=ro)
+    want = orc.readout(want, n, ro, 8, 2)
+    ok = margin > MARGIN
+    np.testing.assert_array_equal(got[ok], want[ok])
+    assert ok.mean() > 0.9
+    del d
+
+
 def test_sample_ghz_full_support(qt, orc):
     n = 12
     psi = np.zeros(1 << n, dtype=np.complex64)

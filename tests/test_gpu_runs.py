@@ -130,6 +130,37 @@ def test_multi_gate_passes_match_single_gate_passes(qt, orc):
     compare_run(qt, orc, circ, 4, k=4, mode=qt.QT_DELAYED, seed=2, S=100)
 
 
+@pytest.mark.parametrize("k", [3, 4])
+def test_noise_model_with_readout_errors(qt, orc, k):
+    """The approximate noise model of Sec. V.B (fSim with coherent errors and Z phases,
+    three-operator decay + dephasing after every gate, 1q and 2q depolarizing) with
+    short T1 / T_phi so that stage 2 flushes happen, plus readout errors on the samples:
+    branch records, states, and samples after readout against the oracle."""
+    circ, ro = qs.noise_model_circuit(3, 3, 8, 4, T1=1e-6, Tphi=1.5e-6)
+    T, S = 12, 60
+    run = qt.Run(qt.Fused(qt.Circuit.from_synth(circ), k), T, seed=6, samples_per_traj=S,
+                 keep_states=True, readout_error=ro)
+    kr, st = run.kraus_indices()
+    ref = orc.run_trajectories(circ, T, seed=6, keep_states=True)
+    smp = run.samples()
+    compared = 0
+    for t in range(T):
+        if np.any(ref["margin"][t] <= MARGIN):
+            continue
+        compared += 1
+        np.testing.assert_array_equal(kr[t], ref["kraus_idx"][t])
+        np.testing.assert_array_equal(st[t], ref["stage"][t])
+        g = run.state(t)
+        assert rel_l2(g, ref["states"][t]) <= STATE_L2
+        want, margin = orc.sample(ref["states"][t], 6, t, S)
+        want = orc.readout(want, circ.num_qubits, ro, 6, t)
+        ok = margin > MARGIN
+        np.testing.assert_array_equal(smp[t][ok], want[ok])
+    assert compared >= 0.75 * T
+    assert run.stats()["flushes"] > 0
+    assert np.any(ref["stage"] == 2) and np.any(ref["kraus_idx"] == 2)   # three-operator stage 2 reached
+
+
 def test_mixture_only_circuit_never_flushes(qt, orc):
     circ = qs.config3_circuit(rows=2, cols=5, depth=10, p=0.05)
     run, _ = compare_run(qt, orc, circ, 8, k=4, mode=qt.QT_DELAYED, S=50)
