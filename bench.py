@@ -264,12 +264,15 @@ def run_ours(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    apply_ms = apply_bytes = launches = passes = flushes = 0
+    apply_ms = apply_bytes = launches = passes = flushes = gate_ops = 0
     ms_w = [0.0] * 8
     passes_w = [0] * 8
+    drift = 0.0
     for i in range(args.steps):
         r = step(args.warmup + i, flags=True)
         s = r.stats()
+        gate_ops += s["gate_ops"]
+        drift = max(drift, float(max(abs(x - 1.0) for x in r.norms())))
         apply_ms += s["apply_ms"]
         apply_bytes += s["apply_bytes"]
         launches += s["kernel_launches"]
@@ -342,6 +345,10 @@ def run_ours(args):
         "clocks": clk,
     }
     line["amplitude_updates_per_s"] = world * passes * float(1 << N_QUBITS) / (ms / 1e3)
+    line["gate_equivalent_updates_per_s"] = world * gate_ops * float(1 << N_QUBITS) / (ms / 1e3)
+    line["error"] = {"norm_drift_max": drift,
+                     "note": "max |<psi|psi> - 1| of the timed trajectories' final states before normalization; "
+                             "parity with the FP64 oracle at this size is checked by tests/test_gpu_fullsize.py"}
     if rank == 0 and not args.no_extras:
         line["delayed_vs_eager"] = delayed_vs_eager(pkg, fused, sh, base + 9_000_000)
         line["bandwidth_probe_n32"] = bandwidth_probe(pkg, qs, sh)
@@ -424,6 +431,17 @@ def run_batch(args):
         ref = oracle.run_trajectory(ccs[i].to_circuit(), oracle.DELAYED, seed=0, traj=j)["state"]
         g = sub.state(j).astype(np.complex128)
         errs.append(float(np.linalg.norm(g - ref) / np.linalg.norm(ref)))
+    # the FP64 oracle on the host cores, on a spread sample of the batch
+    stride_o = max(1, num // 32)
+    sample_o = list(range(0, num, stride_o))
+    t0 = time.perf_counter()
+    for i in sample_o:
+        ref = oracle.run_trajectory(ccs[i].to_circuit(), oracle.DELAYED, seed=0, traj=i)
+        oracle.sample(ref["state"], 0, i, SAMPLES)
+    t_orc = time.perf_counter() - t0
+    cpu = {"value": len(sample_o) / t_orc, "unit": UNIT, "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+           "sample": f"every {stride_o}th circuit ({len(sample_o)} trajectories with {SAMPLES} samples), FP64 "
+                     f"oracle, {t_orc:.1f} s"}
     st = batch.stats()
     amps = np.array([1 << c.num_qubits for c in ccs], dtype=np.float64)
     nf = np.array([f.info()["num_fused"] for f in fused], dtype=np.float64)
@@ -445,6 +463,7 @@ def run_batch(args):
                                  f"one trajectory at a time on the same GPU, scaled by {stride}"},
         "speedup_vs_plain": batched / plain,
         "amplitude_updates_per_s": amp_updates,
+        "cpu_baseline": cpu,
         "effective_bandwidth": {"achieved": eff_gbs, "peak": peak, "unit": "GB/s", "frac": eff_gbs / peak,
                                 "peak_kind": peak_kind,
                                 "note": "algorithmic bytes (16 B x 2^n per fused pass) / kernel time; "
@@ -576,17 +595,26 @@ def run_precision(args):
     # error against the FP64 oracle at n = 26
     c26 = qs.config3_circuit(rows=2, cols=13, depth=24)
     f26 = pkg.Fused(pkg.Circuit.from_synth(c26), 6)
+    T26 = 4
     t0 = time.perf_counter()
-    ref = oracle.run_trajectory(c26, oracle.DELAYED, seed=0, traj=0)["state"]
+    refs = [oracle.run_trajectory(c26, oracle.DELAYED, seed=0, traj=t)["state"] for t in range(T26)]
     t_orc = time.perf_counter() - t0
     errs = {}
     for name, prec in (("tf32x3", pkg.QT_TF32X3), ("fp32", pkg.QT_FP32)):
-        r = pkg.Run(f26, 1, seed=0, precision=prec, keep_states=True, stream=sh)
-        g = r.state(0).astype(np.complex128)
-        errs[name] = {"rel_l2": float(np.linalg.norm(g - ref) / np.linalg.norm(ref)),
-                      "fidelity": float(abs(np.vdot(ref, g)) ** 2 / (np.vdot(g, g).real * np.vdot(ref, ref).real))}
+        r = pkg.Run(f26, T26, seed=0, precision=prec, keep_states=True, stream=sh)
+        l2, fid = [], []
+        for t in range(T26):
+            g = r.state(t).astype(np.complex128)
+            ref = refs[t]
+            l2.append(float(np.linalg.norm(g - ref) / np.linalg.norm(ref)))
+            fid.append(float(abs(np.vdot(ref, g)) ** 2 / (np.vdot(g, g).real * np.vdot(ref, ref).real)))
+        errs[name] = {"trajectories": T26, "rel_l2_max": max(l2), "rel_l2_mean": float(np.mean(l2)),
+                      "fidelity_min": min(fid)}
     out["error_n26"] = errs
     out["oracle_n26_s"] = t_orc
+    out["cpu_baseline"] = {"value": T26 / t_orc, "unit": "trajectories/s (n = 26)",
+                           "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                           "sample": f"{T26} trajectories of the 26-qubit error workload (FP64, unfused)"}
     # throughput and norm drift at n = 32
     c32 = qs.config3_circuit()
     f32 = pkg.Fused(pkg.Circuit.from_synth(c32), 6)
@@ -703,13 +731,43 @@ def run_chain10(args):
             assert smp.shape == (T, SAMPLES)
         t = statistics.median(times[args.warmup:])
         res[name] = {"traj_per_s": T / t, "ms_per_64_traj": t * 1e3}
+    # the FP64 oracle on the host cores: all 64 trajectories with their samples
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    ref = oracle.run_trajectories(circ, T, seed=0, traj0=0, keep_states=True)
+    for t in range(T):
+        oracle.sample(ref["states"][t], 0, t, SAMPLES)
+    t_orc = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0))
+    # parity of the batched records against it (ties, margin <= 1e-6, are not compared)
+    b = pkg.Batch([f] * T).run(seed=0, first_traj=0, samples_per_traj=SAMPLES, keep_states=True, stream=sh)
+    smp = b.samples()
+    errs, bad_rec, bad_smp, compared = [], 0, 0, 0
+    for t in range(T):
+        if np.any(ref["margin"][t] <= 1e-6):
+            continue
+        compared += 1
+        kr, _ = b.kraus_indices(t)
+        bad_rec += int(np.sum(kr != ref["kraus_idx"][t]))
+        g = b.state(t).astype(np.complex128)
+        w = ref["states"][t]
+        errs.append(float(np.linalg.norm(g - w) / np.linalg.norm(w)))
+        want, margin = oracle.sample(w, 0, t, SAMPLES)
+        ok = margin > 1e-6
+        bad_smp += int(np.sum(smp[t][ok] != want[ok]))
     line = {"metric": METRIC, "value": res["batched"]["traj_per_s"], "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "form": "chain10",
             "data": "synthetic", "dtype": "f32",
             "config": {"workload": "chain10: 10-qubit chain, depth 16, depolarizing 1e-3 / 1e-2, amplitude "
                                    "damping 1e-3, 64 trajectories x 100 samples, fused k=2"},
             "plain": res["plain"], "batched": res["batched"],
-            "speedup_vs_plain": res["batched"]["traj_per_s"] / res["plain"]["traj_per_s"]}
+            "speedup_vs_plain": res["batched"]["traj_per_s"] / res["plain"]["traj_per_s"],
+            "cpu_baseline": {"value": T / t_orc, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"all {T} trajectories with {SAMPLES} samples each (FP64, unfused, "
+                                       f"OpenMP over trajectories), {t_orc:.2f} s"},
+            "parity": {"trajectories_compared": compared, "branch_record_mismatches": bad_rec,
+                       "sample_mismatches": bad_smp, "state_rel_l2_max": max(errs) if errs else None}}
     print(json.dumps(line), flush=True)
     return 0
 
