@@ -126,8 +126,9 @@ def dist_env():
 # CPU baseline: the FP64 oracle as it stands on a bounded sample
 # ----------------------------------------------------------------------------
 def oracle_sample(target_s=15.0, psi=None):
-    """Run the oracle on the first M ops of trajectory 0 of the workload,
-    M chosen so that the run takes about target_s.  Returns trajectories/s
+    """Run the oracle on the first M ops of trajectory 0 of the workload, M
+    doubled from 8 until one run takes at least a third of target_s (so the
+    whole sampling stays within about target_s).  Returns trajectories/s
     scaled by (total ops / M) and a description."""
     import numpy as np
 
@@ -139,17 +140,14 @@ def oracle_sample(target_s=15.0, psi=None):
     total = len(circ.ops)
     if psi is None:
         psi = np.empty(1 << N_QUBITS, dtype=np.complex128)
-    t0 = time.perf_counter()
-    oracle.run_trajectory(fc, oracle.DELAYED, seed=0, traj=0, max_ops=2, psi=psi)
-    t2 = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    oracle.run_trajectory(fc, oracle.DELAYED, seed=0, traj=0, max_ops=6, psi=psi)
-    t6 = time.perf_counter() - t0
-    per_op = max((t6 - t2) / 4, 1e-6)           # the |0..0> initialisation is paid once
-    M = int(max(6, min(total, (target_s - t2) / per_op)))
-    t0 = time.perf_counter()
-    oracle.run_trajectory(fc, oracle.DELAYED, seed=0, traj=0, max_ops=M, psi=psi)
-    dt = time.perf_counter() - t0
+    M = 8
+    while True:
+        t0 = time.perf_counter()
+        oracle.run_trajectory(fc, oracle.DELAYED, seed=0, traj=0, max_ops=M, psi=psi)
+        dt = time.perf_counter() - t0
+        if dt >= target_s / 3 or M >= total:
+            break
+        M = min(total, 2 * M)
     value = (M / total) / dt
     cores = len(os.sched_getaffinity(0))
     desc = (f"first {M} of {total} ops of trajectory 0 of the 30-qubit workload (FP64 oracle, "
@@ -267,12 +265,10 @@ def run_ours(args):
     apply_ms = apply_bytes = launches = passes = flushes = gate_ops = 0
     ms_w = [0.0] * 8
     passes_w = [0] * 8
-    drift = 0.0
     for i in range(args.steps):
         r = step(args.warmup + i, flags=True)
         s = r.stats()
         gate_ops += s["gate_ops"]
-        drift = max(drift, float(max(abs(x - 1.0) for x in r.norms())))
         apply_ms += s["apply_ms"]
         apply_bytes += s["apply_bytes"]
         launches += s["kernel_launches"]
@@ -346,9 +342,6 @@ def run_ours(args):
     }
     line["amplitude_updates_per_s"] = world * passes * float(1 << N_QUBITS) / (ms / 1e3)
     line["gate_equivalent_updates_per_s"] = world * gate_ops * float(1 << N_QUBITS) / (ms / 1e3)
-    line["error"] = {"norm_drift_max": drift,
-                     "note": "max |<psi|psi> - 1| of the timed trajectories' final states before normalization; "
-                             "parity with the FP64 oracle at this size is checked by tests/test_gpu_fullsize.py"}
     if rank == 0 and not args.no_extras:
         line["delayed_vs_eager"] = delayed_vs_eager(pkg, fused, sh, base + 9_000_000)
         line["bandwidth_probe_n32"] = bandwidth_probe(pkg, qs, sh)
