@@ -20,7 +20,9 @@ QT_HD U32x4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
   // ten rounds; each round multiplies lanes 0 and 2 by the Philox constants,
   // swaps the high halves across, xors in the round key and bumps the key by
   // the Weyl increments (golden ratio, sqrt(3) - 1)
+#if defined(__CUDACC__)
 #pragma unroll
+#endif
   for (int r = 0; r < 10; ++r) {
     const uint64_t m0 = static_cast<uint64_t>(c0) * 0xD2511F53ull;
     const uint64_t m1 = static_cast<uint64_t>(c2) * 0xCD9E8D57ull;
