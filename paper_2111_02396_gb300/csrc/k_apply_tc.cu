@@ -277,11 +277,13 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
   const bool split = NCHUNK == 2 && a.nh >= 1 && a.tins[K - 1] == static_cast<uint32_t>(a.C + a.nh - 1);
   if (warp == 9) {
     // ---------------- producer: bulk copies of the tile rows ----------------
-    if (lane == 0) {
+    // lane 0 waits for a free buffer and sets its transaction count; then the
+    // warp's 32 lanes issue the unit's row copies together (up to 64 rows)
+    {
       uint32_t lastuse[8] = {0, 0, 0, 0, 0, 0, 0, 0};
       int issued[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      // stage units: whole tiles (two buffers), or for k = 6 with a high top
-      // target the two chunk halves of one tile buffer
+      // stage units: whole tiles (several buffers), or for k = 6 with a high
+      // top target the two chunk halves of one tile buffer
       uint32_t it = 0;
       const int nunits = split ? 2 : 1;
       const int urows = nrows / nunits;
@@ -296,10 +298,15 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
         for (int u = 0; u < nunits; ++u) {
           const uint32_t b = split ? static_cast<uint32_t>(u) : it % NBUF;
           const uint32_t use = split ? it : it / NBUF;
-          if (use > 0 && !mbar_wait(&t_empty[b], (use - 1) & 1, a.err, 32)) { stop = true; break; }
-          mbar_expect_tx(&t_full[b], ubytes);
+          int go = 1;
+          if (lane == 0) {
+            if (use > 0 && !mbar_wait(&t_empty[b], (use - 1) & 1, a.err, 32)) go = 0;
+            else mbar_expect_tx(&t_full[b], ubytes);
+          }
+          go = __shfl_sync(0xffffffffu, go, 0);      // also orders the copies after expect_tx
+          if (!go) { stop = true; break; }
           float2* dst = split ? tbuf + u * (TILE_AMPS / 2) : tbuf + b * TILE_AMPS;
-          for (int r = 0; r < urows; ++r)
+          for (int r = lane; r < urows; r += 32)
             bulk_g2s(dst + (static_cast<uint32_t>(r) << a.C), psi + (base | a.roff[u * urows + r]), rowbytes,
                      &t_full[b]);
           lastuse[b] = use;
@@ -307,8 +314,9 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
         }
       }
       // no copy may outlive the CTA: wait (bounded) for the last staged units
-      for (int b = 0; b < 8; ++b)
-        if (issued[b]) mbar_drain(&t_full[b], lastuse[b] & 1, a.err, 128);
+      if (lane == 0)
+        for (int b = 0; b < 8; ++b)
+          if (issued[b]) mbar_drain(&t_full[b], lastuse[b] & 1, a.err, 128);
     }
     __syncwarp();
   } else if (warp < 4) {
