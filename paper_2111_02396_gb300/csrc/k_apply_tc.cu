@@ -382,16 +382,22 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
         const uint32_t h = a.hins[j];
         base = ((base >> h) << (h + 1)) | (base & ((1ull << h) - 1ull));
       }
+      // accumulator columns in blocks of 32, two loads in flight per wait
 #pragma unroll
-      for (int cb = 0; cb < N / 32; ++cb) {
-        uint32_t v[32];
-        tmem_ld32(tmem + lane_base + d_col0 + db * N + cb * 32, v);
+      for (int cb = 0; cb < N / 32; cb += 2) {
+        uint32_t v[2][32];
+        tmem_ld32(tmem + lane_base + d_col0 + db * N + cb * 32, v[0]);
+        if (cb + 1 < N / 32) tmem_ld32(tmem + lane_base + d_col0 + db * N + (cb + 1) * 32, v[1]);
         tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const uint32_t l = sbase | a.moff[cb * 16 + j];
-          __stcs(psi + (base | a.roff[l >> a.C] | (l & rowmask)),
-                 make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1])));
+        for (int h = 0; h < 2; ++h) {
+          if (cb + h >= N / 32) break;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const uint32_t l = sbase | a.moff[(cb + h) * 16 + j];
+            __stcs(psi + (base | a.roff[l >> a.C] | (l & rowmask)),
+                   make_float2(__uint_as_float(v[h][2 * j]), __uint_as_float(v[h][2 * j + 1])));
+          }
         }
       }
       fence_before();
