@@ -342,7 +342,7 @@ def run_ours(args):
     }
     line["amplitude_updates_per_s"] = world * passes * float(1 << N_QUBITS) / (ms / 1e3)
     line["gate_equivalent_updates_per_s"] = world * gate_ops * float(1 << N_QUBITS) / (ms / 1e3)
-    if rank == 0 and not args.no_extras:
+    if rank == 0 and world == 1 and not args.no_extras:
         line["delayed_vs_eager"] = delayed_vs_eager(pkg, fused, sh, base + 9_000_000)
         line["bandwidth_probe_n32"] = bandwidth_probe(pkg, qs, sh)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
