@@ -14,7 +14,8 @@
 // fused like gates of their qubits ("slots"): the operator in a slot is
 // chosen per trajectory.  Which candidate a grows by is a choice the paper
 // leaves open: two rules are run (most shared qubits; most later gates
-// absorbed) and the plan with the lower modelled pass time is kept.
+// absorbed), each on the circuit and on its time reversal, and the plan
+// with the lower modelled pass time is kept.
 #include <algorithm>
 #include <bit>
 #include <new>
@@ -117,22 +118,32 @@ qt_status fuse_circuit(const Circuit& c, uint32_t kmax, Fused& f) {
     if (op.kind == QT_OP_GATE) f.gate_ops++;
   }
   const uint64_t all_mask = (c.n >= 64) ? ~0ull : ((1ull << c.n) - 1ull);
-  // two plans, one per candidate rule; keep the one with the lower pass cost
+  // four plans: each candidate rule on the circuit and on its time reversal;
+  // keep the one with the lower pass cost.  A plan of the reversed circuit,
+  // taken in reverse order with each gate's members in circuit order, is a
+  // plan of the circuit: every reordering it implies swaps operations on
+  // disjoint qubits.
   std::vector<Work> best;
   double best_cost = 0.0;
-  for (Pick pick : {Pick::kShared, Pick::kLookahead}) {
-    std::vector<Work> w = g;
-    for (int phase = 0; phase < 2; ++phase)
-      for (size_t a = 0; a < w.size(); ++a)
-        if (w[a].alive) grow(w, a, static_cast<int>(kmax), all_mask, phase == 1, pick);
-    double cost = 0.0;
-    for (const Work& x : w)
-      if (x.alive) cost += pass_cost(popc(x.mask));
-    if (best.empty() || cost < best_cost) {
-      best = std::move(w);
-      best_cost = cost;
+  for (int reversed = 0; reversed < 2; ++reversed)
+    for (Pick pick : {Pick::kShared, Pick::kLookahead}) {
+      std::vector<Work> w = g;
+      if (reversed) std::reverse(w.begin(), w.end());
+      for (int phase = 0; phase < 2; ++phase)
+        for (size_t a = 0; a < w.size(); ++a)
+          if (w[a].alive) grow(w, a, static_cast<int>(kmax), all_mask, phase == 1, pick);
+      double cost = 0.0;
+      for (const Work& x : w)
+        if (x.alive) cost += pass_cost(popc(x.mask));
+      if (best.empty() || cost < best_cost - 1e-9) {
+        if (reversed) {
+          std::reverse(w.begin(), w.end());
+          for (Work& x : w) std::sort(x.members.begin(), x.members.end());
+        }
+        best = std::move(w);
+        best_cost = cost;
+      }
     }
-  }
   g = std::move(best);
 
   f.gate_of_op.assign(c.ops.size(), 0);
