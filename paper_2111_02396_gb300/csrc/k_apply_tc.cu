@@ -214,12 +214,14 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
   constexpr int MPC = CR / 2;                // members per chunk (16 or 32)
   constexpr int TILE_AMPS = kTileSets * NM;
   constexpr int NBUF = K >= 6 ? 1 : (K == 5 ? 4 : 8);   // staged tiles (bytes in flight)
+  constexpr int RING = 3;                    // split mode: chunk-half buffers in a ring
+  constexpr int TBUF_AMPS = (NBUF * TILE_AMPS > RING * TILE_AMPS / 2) ? NBUF * TILE_AMPS : RING * TILE_AMPS / 2;
   constexpr uint32_t IDESC = idesc_tf32(kTileSets, N);
   extern __shared__ __align__(1024) uint8_t smem[];
   float* bhi = reinterpret_cast<float*>(smem);
   float* blo = bhi + N * N;
-  float2* tbuf = reinterpret_cast<float2*>(blo + N * N);          // NBUF tiles
-  uint64_t* bars = reinterpret_cast<uint64_t*>(tbuf + NBUF * TILE_AMPS);
+  float2* tbuf = reinterpret_cast<float2*>(blo + N * N);          // NBUF tiles, or RING chunk halves
+  uint64_t* bars = reinterpret_cast<uint64_t*>(tbuf + TBUF_AMPS);
   uint64_t* a_full = bars;         // [2]
   uint64_t* a_empty = bars + 2;    // [2]
   uint64_t* d_full = bars + 4;     // [2]
@@ -296,8 +298,10 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
           base = ((base >> h) << (h + 1)) | (base & ((1ull << h) - 1ull));
         }
         for (int u = 0; u < nunits; ++u) {
-          const uint32_t b = split ? static_cast<uint32_t>(u) : it % NBUF;
-          const uint32_t use = split ? it : it / NBUF;
+          // split: chunk half g = 2 it + u goes to ring slot g % RING
+          const uint32_t g = 2u * it + static_cast<uint32_t>(u);
+          const uint32_t b = split ? g % RING : it % NBUF;
+          const uint32_t use = split ? g / RING : it / NBUF;
           int go = 1;
           if (lane == 0) {
             if (use > 0 && !mbar_wait(&t_empty[b], (use - 1) & 1, a.err, 32)) go = 0;
@@ -305,7 +309,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
           }
           go = __shfl_sync(0xffffffffu, go, 0);      // also orders the copies after expect_tx
           if (!go) { stop = true; break; }
-          float2* dst = split ? tbuf + u * (TILE_AMPS / 2) : tbuf + b * TILE_AMPS;
+          float2* dst = split ? tbuf + b * (TILE_AMPS / 2) : tbuf + b * TILE_AMPS;
           for (int r = lane; r < urows; r += 32)
             bulk_g2s(dst + (static_cast<uint32_t>(r) << a.C), psi + (base | a.roff[u * urows + r]), rowbytes,
                      &t_full[b]);
@@ -335,7 +339,15 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
       if (!split && !mbar_wait(&t_full[b], (it / NBUF) & 1, a.err, 64)) break;
       const float2* tb = tbuf + b * TILE_AMPS;
       for (int c = 0; c < NCHUNK; ++c, ++chunk_iter) {
-        if (split && !mbar_wait(&t_full[c], it & 1, a.err, 64)) { ok = false; break; }
+        // split: this chunk half sits in ring slot chunk_iter % RING; its members'
+        // tile offsets carry the top target bit (TILE_AMPS / 2) when c = 1
+        const uint32_t rs = chunk_iter % RING;
+        uint32_t tsub = 0;                   // tile offset of the staged unit's first amplitude
+        if (split) {
+          if (!mbar_wait(&t_full[rs], (chunk_iter / RING) & 1, a.err, 64)) { ok = false; break; }
+          tb = tbuf + rs * (TILE_AMPS / 2);
+          tsub = static_cast<uint32_t>(c) * (TILE_AMPS / 2);
+        }
         const uint32_t slot = chunk_iter & 1;
         const uint32_t use = chunk_iter >> 1;
         if (use > 0 && !mbar_wait(&a_empty[slot], (use - 1) & 1, a.err, 1)) { ok = false; break; }
@@ -344,7 +356,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
         for (int half = 0; half < MPC / 16; ++half) {
 #pragma unroll
           for (int m = 0; m < 16; ++m) {
-            const float2 v = tb[sbase | a.moff[c * MPC + half * 16 + m]];
+            const float2 v = tb[(sbase | a.moff[c * MPC + half * 16 + m]) - tsub];
             const uint32_t hr = to_tf32(v.x), hm = to_tf32(v.y);
             hi[2 * m] = hr;
             hi[2 * m + 1] = hm;
@@ -358,7 +370,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
         tmem_wait_st();
         fence_before();
         mbar_arrive(&a_full[slot]);
-        if (split) mbar_arrive(&t_empty[c]);   // done reading this chunk's half
+        if (split) mbar_arrive(&t_empty[rs]);  // done reading this chunk half
       }
       if (!split && ok) mbar_arrive(&t_empty[b]);   // done reading the staged tile
     }
@@ -463,8 +475,9 @@ static cudaError_t launch_tc_k(float2* psi, int n, const uint32_t* targets, cons
   constexpr int NM = 1 << K;
   constexpr int N = 2 * NM;
   constexpr int NBUF = K >= 6 ? 1 : (K == 5 ? 4 : 8);
-  const size_t smem = 2 * sizeof(float) * N * N + NBUF * sizeof(float2) * tc::kTileSets * NM +
-                      24 * sizeof(uint64_t) + 16;
+  constexpr int TILE_AMPS = tc::kTileSets * NM;
+  constexpr int TBUF_AMPS = (NBUF * TILE_AMPS > 3 * TILE_AMPS / 2) ? NBUF * TILE_AMPS : 3 * TILE_AMPS / 2;
+  const size_t smem = 2 * sizeof(float) * N * N + TBUF_AMPS * sizeof(float2) + 24 * sizeof(uint64_t) + 16;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [&] {
