@@ -126,7 +126,8 @@ struct TileArgs {
   float e[1 << K][1 << K];    // Re U + Im U
   float f[1 << K][1 << K];    // Im U - Re U
   uint64_t roff[1 << K];      // memory offset of tile row r
-  uint32_t moff[1 << K];      // tile-local offset of member m
+  uint64_t poff[1 << K];      // memory offset of tile index 256 c (chunk c of every thread)
+  uint32_t smoff[1 << K];     // swizzled tile-local offset of member m
   uint32_t tins[K];           // tile-local target positions, ascending
   uint32_t hins[K];           // memory positions of the high targets, ascending
   int nh;                     // number of high targets
@@ -136,18 +137,28 @@ struct TileArgs {
 
 __device__ __forceinline__ uint32_t swz(uint32_t l) { return l ^ ((l >> 4) & 15u); }
 
-// RU: unroll factor of the row loop.  At K = 4 the rows are fully unrolled
-// (every matrix entry a fixed constant-bank operand) under a 6-CTA occupancy
-// bound (80 registers); for the other widths rows go two at a time.
+// RU: unroll factor of the row loop; MINB: CTAs per SM that the register
+// allocation must allow.  Rows go two at a time (the matrix entries of a row
+// pair come in through uniform constant loads).  At K = 4 the kernel is
+// issue-bound, and an 8-CTA bound (61 registers, no spills) gives the
+// scheduler the most warps to choose from; a full row unroll keeps more
+// values live than even 255 registers hold.
+//
+// Index arithmetic is hoisted out of the per-amplitude work with two
+// identities.  The swizzle distributes over an OR of disjoint bit sets,
+// swz(x | y) = swz(x) ^ swz(y), so member m of the thread's set sits at
+// swz(sbase) ^ smoff[m] with smoff[m] = swz(moff[m]) precomputed.  The map
+// from a tile index to its memory offset deposits bits (the row bits go to
+// the high-target positions), so it too distributes over disjoint bits:
+// thread t's chunk c (tile index 2t + 256c) is at offset(2t) | poff[c].
 template <int K, int RU = 2, int MINB = 1>
 __global__ void __launch_bounds__(kTileThreads, MINB) k_apply_tile(float2* __restrict__ psi,
                                                              const __grid_constant__ TileArgs<K> a) {
   constexpr int M = 1 << K;
   constexpr int TILE = kTileThreads * M;       // amplitudes per tile
-  constexpr int CHUNKS = TILE / 2;             // float4 chunks per tile
+  constexpr int NCH = TILE / 2 / kTileThreads; // float4 chunks per thread
   __shared__ __align__(16) float2 sm[TILE];
   const uint32_t tid = threadIdx.x;
-  const uint32_t rowmask = (1u << a.C) - 1u;
   // this thread's gather set inside the tile (same for every tile)
   uint32_t sbase = tid;
 #pragma unroll
@@ -155,6 +166,7 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_apply_tile(float2* __res
     const uint32_t t = a.tins[b];
     sbase = ((sbase >> t) << (t + 1)) | (sbase & ((1u << t) - 1u));
   }
+  const uint32_t ss = swz(sbase);
   // one tile per CTA: a loop over tiles would make the matrix entries
   // loop-invariant, and the compiler would then hold them in registers
   {
@@ -164,27 +176,27 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_apply_tile(float2* __res
       const uint32_t h = a.hins[j];
       base = ((base >> h) << (h + 1)) | (base & ((1ull << h) - 1ull));
     }
+    const uint32_t l0 = 2u * tid;
+    float2* const pt = psi + (base | a.roff[l0 >> a.C] | (l0 & ((1u << a.C) - 1u)));
+    // bits 4..7 of the tile index 2t + 256c are bits 3..6 of t, so the
+    // swizzle of both amplitudes of a chunk is the same for every c
+    const uint32_t fl = (tid >> 3) & 15u;
+    const uint32_t s0 = l0 ^ fl, s1 = (l0 + 1u) ^ fl;
     // load rows -> shared (coalesced 128-bit)
-    float4 buf[CHUNKS / kTileThreads];
+    float4 buf[NCH];
 #pragma unroll
-    for (int i = 0; i < CHUNKS / kTileThreads; ++i) {
-      const uint32_t l = 2u * (tid + i * kTileThreads);
-      buf[i] = __ldcs(reinterpret_cast<const float4*>(psi + (base | a.roff[l >> a.C] | (l & rowmask))));
-    }
+    for (int c = 0; c < NCH; ++c) buf[c] = __ldcs(reinterpret_cast<const float4*>(pt + a.poff[c]));
 #pragma unroll
-    for (int i = 0; i < CHUNKS / kTileThreads; ++i) {
-      const uint32_t l = 2u * (tid + i * kTileThreads);
-      const uint32_t fl = (l >> 4) & 15u;
-      float4 v = buf[i];
-      if (fl & 1u) v = make_float4(v.z, v.w, v.x, v.y);
-      *reinterpret_cast<float4*>(&sm[(l ^ fl) & ~1u]) = v;
+    for (int c = 0; c < NCH; ++c) {
+      sm[s0 + 256u * c] = make_float2(buf[c].x, buf[c].y);
+      sm[s1 + 256u * c] = make_float2(buf[c].z, buf[c].w);
     }
     __syncthreads();
     // one gather set per thread
     float va[M], vb[M], vs[M];
 #pragma unroll
     for (int m = 0; m < M; ++m) {
-      const float2 v = sm[swz(sbase | a.moff[m])];
+      const float2 v = sm[ss ^ a.smoff[m]];
       va[m] = v.x;
       vb[m] = v.y;
       vs[m] = v.x + v.y;
@@ -201,17 +213,14 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_apply_tile(float2* __res
         r = fmaf(a.e[j][m], vb[m], r);
         im = fmaf(a.f[j][m], va[m], im);
       }
-      sm[swz(sbase | a.moff[j])] = make_float2(t - r, t + im);
+      sm[ss ^ a.smoff[j]] = make_float2(t - r, t + im);
     }
     __syncthreads();
     // shared -> rows (coalesced 128-bit)
 #pragma unroll
-    for (int i = 0; i < CHUNKS / kTileThreads; ++i) {
-      const uint32_t l = 2u * (tid + i * kTileThreads);
-      const uint32_t fl = (l >> 4) & 15u;
-      float4 v = *reinterpret_cast<const float4*>(&sm[(l ^ fl) & ~1u]);
-      if (fl & 1u) v = make_float4(v.z, v.w, v.x, v.y);
-      __stcs(reinterpret_cast<float4*>(psi + (base | a.roff[l >> a.C] | (l & rowmask))), v);
+    for (int c = 0; c < NCH; ++c) {
+      const float2 x = sm[s0 + 256u * c], y = sm[s1 + 256u * c];
+      __stcs(reinterpret_cast<float4*>(pt + a.poff[c]), make_float4(x.x, x.y, y.x, y.y));
     }
     __syncthreads();
   }
@@ -254,7 +263,7 @@ static cudaError_t launch_tile(float2* psi, int n, const uint32_t* targets, cons
     uint32_t o = 0;
     for (int b = 0; b < K; ++b)
       if ((m >> b) & 1) o |= 1u << tpos[b];
-    a.moff[m] = o;
+    a.smoff[m] = o ^ ((o >> 4) & 15u);
   }
   for (int r = 0; r < M; ++r) {
     uint64_t o = 0;
@@ -262,9 +271,14 @@ static cudaError_t launch_tile(float2* psi, int n, const uint32_t* targets, cons
       if ((r >> j) & 1) o |= 1ull << a.hins[j];
     a.roff[r] = r < (1 << nh) ? o : 0;
   }
+  // chunk c of every thread starts at tile index 256 c (< 2^(7+K))
+  for (int c = 0; c < M; ++c) {
+    const uint32_t l = 256u * static_cast<uint32_t>(c);
+    a.poff[c] = c < M / 2 ? (a.roff[l >> C] | (l & ((1u << C) - 1u))) : 0;
+  }
   a.num_tiles = 1ull << (n - C - nh);
   if constexpr (K == 4)
-    k_apply_tile<4, 16, 6><<<static_cast<unsigned>(a.num_tiles), kTileThreads, 0, st>>>(psi, a);
+    k_apply_tile<4, 2, 8><<<static_cast<unsigned>(a.num_tiles), kTileThreads, 0, st>>>(psi, a);
   else
     k_apply_tile<K><<<static_cast<unsigned>(a.num_tiles), kTileThreads, 0, st>>>(psi, a);
   return cudaGetLastError();
