@@ -39,8 +39,8 @@ WORKLOAD = ("grid30: 5x6 grid, depth 20, sqrtX/sqrtY/sqrtW + CZ, amplitude dampi
 # DRAM bytes per launch of the fused-gate kernel from an ncu capture, keyed by
 # the SHA-256 of the kernel source it was taken on (null once the source changes).
 KNOWN_TRAFFIC = {
-    # k_apply_tile<4, 2, 8>: 4.234 GB per launch at n = 28 (dram read + write), x4 for n = 30
-    "7cd0722e4de5d16b": 4 * (2147512832 + 2086149888),
+    # k_apply_tile<4, 4, 8>: 4.243 GB per launch at n = 28 (dram read + write), x4 for n = 30
+    "47cecb13fb653b49": 4 * (2147521280 + 2095411200),
 }
 
 

@@ -96,9 +96,9 @@ bool grow(std::vector<Work>& g, size_t a, int kmax, uint64_t all_mask, bool allo
 
 // relative device time of one pass of a fused gate of width w (measured
 // rates of the fused-gate kernels at 30 qubits: 6.5 TB/s up to width 3,
-// 5.5 at width 4, and 4.5 and 3.9 for the tensor-core kernel at widths 5, 6)
+// 5.9 at width 4, and 4.5 and 3.9 for the tensor-core kernel at widths 5, 6)
 double pass_cost(int w) {
-  static const double c[7] = {1.0, 1.0, 1.0, 1.0, 1.2, 1.45, 1.7};
+  static const double c[7] = {1.0, 1.0, 1.0, 1.0, 1.1, 1.45, 1.7};
   return c[w < 7 ? w : 6];
 }
 

@@ -16,13 +16,14 @@
 // conflicts.  Each thread then gathers one set, multiplies, and scatters
 // it back; the tile is stored with the same coalesced pattern.
 //
-// The matrix is a __grid_constant__ kernel parameter: with the loops over
-// rows and columns unrolled every matrix entry is a constant-bank operand
-// of the FMA that uses it.  The complex products use the three-multiply
-// form: with U = c + i d and v = a + i b, precomputing e = c + d and
-// f = d - c per entry and s = a + b per amplitude,
+// The matrix is a __grid_constant__ kernel parameter: its entries reach the
+// FMAs through uniform registers loaded from the constant bank.  The complex
+// products use the three-multiply form: with U = c + i d and v = a + i b,
+// precomputing e = c + d and f = d - c per entry and s = a + b per amplitude,
 //   Re(U v) = sum c s - sum b e,   Im(U v) = sum c s + sum a f,
-// i.e. 3 FFMA per complex multiply-add instead of 4.
+// i.e. 3 FMA per complex multiply-add instead of 4.  The two sums that
+// share an entry pair, (sum c s, sum e b), run as one packed FP32x2 FMA on
+// the (c, e) pair, so a complex multiply-add issues 2 instructions.
 //
 // k_apply (direct, for states smaller than one tile): one thread per
 // gather set (or per pair of sets that differ in bit 0), members loaded
@@ -120,16 +121,17 @@ int sm_count() {
 // ---------------------------------------------------------------------------
 constexpr int kTileThreads = 128;       // = gather sets per tile
 
+// 16-byte aligned so that the matrix pairs sit on aligned constant-bank words
 template <int K>
-struct TileArgs {
-  float c[1 << K][1 << K];    // Re U
-  float e[1 << K][1 << K];    // Re U + Im U
+struct alignas(16) TileArgs {
+  float2 ce[1 << K][1 << K];  // (Re U, Re U + Im U)
   float f[1 << K][1 << K];    // Im U - Re U
   uint64_t roff[1 << K];      // memory offset of tile row r
   uint64_t poff[1 << K];      // memory offset of tile index 256 c (chunk c of every thread)
   uint32_t smoff[1 << K];     // swizzled tile-local offset of member m
   uint32_t tins[K];           // tile-local target positions, ascending
   uint32_t hins[K];           // memory positions of the high targets, ascending
+  uint8_t swzt[16];           // swizzle table: slot = l ^ swzt[(l >> 4) & 15]
   int nh;                     // number of high targets
   int C;                      // contiguous low bits per row
   uint64_t num_tiles;
@@ -137,12 +139,46 @@ struct TileArgs {
 
 __device__ __forceinline__ uint32_t swz(uint32_t l) { return l ^ ((l >> 4) & 15u); }
 
+// The swizzle of the tile kernel is chosen per launch.  It XORs a linear
+// (GF(2)) image of index bits 4..7 into bits 0..3, slot = l ^ G(l >> 4 & 15).
+// A half-warp's 16 lanes differ in the 4 lowest non-target tile positions;
+// those below 4 stay put, and G maps those in 4..7 onto the target positions
+// below 4, so every 8-byte gather and scatter of a half-warp hits 16
+// distinct bank pairs, whatever the targets.  (No fixed map does this for
+// every pattern: the single-target cases force every entry of G to 1.)  The
+// image of bit 4 also sets bit 0, which keeps the coalesced staging stores
+// (lane t writes index 2t) conflict-free.
+__device__ __forceinline__ uint32_t swz_t(uint32_t l, const uint8_t* t) { return l ^ t[(l >> 4) & 15u]; }
+
+static void swizzle_table(const uint32_t* tpos, int K, uint8_t* tab) {
+  uint32_t tmask = 0;
+  for (int b = 0; b < K; ++b) tmask |= 1u << tpos[b];
+  int lane[4], nl = 0;
+  for (uint32_t p = 0; nl < 4; ++p)
+    if (!((tmask >> p) & 1u)) lane[nl++] = static_cast<int>(p);
+  uint32_t g[4] = {1u, 2u, 4u, 8u};    // image of bit 4 + i (the fixed map)
+  if (lane[3] < 8) {
+    int low = 0;                       // target positions below 4, ascending
+    for (int i = 0; i < 4; ++i)
+      if (lane[i] >= 4) {
+        while (!((tmask >> low) & 1u)) ++low;
+        g[lane[i] - 4] = 1u << low++;
+      }
+  }
+  g[0] |= 1u;
+  for (int x = 0; x < 16; ++x) {
+    uint32_t v = 0;
+    for (int i = 0; i < 4; ++i)
+      if ((x >> i) & 1) v ^= g[i];
+    tab[x] = static_cast<uint8_t>(v);
+  }
+}
+
 // RU: unroll factor of the row loop; MINB: CTAs per SM that the register
-// allocation must allow.  Rows go two at a time (the matrix entries of a row
-// pair come in through uniform constant loads).  At K = 4 the kernel is
-// issue-bound, and an 8-CTA bound (61 registers, no spills) gives the
-// scheduler the most warps to choose from; a full row unroll keeps more
-// values live than even 255 registers hold.
+// allocation must allow.  At K = 4 the kernel is issue-bound: rows go four
+// at a time under an 8-CTA bound (64 registers), which gives the scheduler
+// the most warps to choose from; a full row unroll keeps more values live
+// than even 255 registers hold.
 //
 // Index arithmetic is hoisted out of the per-amplitude work with two
 // identities.  The swizzle distributes over an OR of disjoint bit sets,
@@ -166,7 +202,7 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_apply_tile(float2* __res
     const uint32_t t = a.tins[b];
     sbase = ((sbase >> t) << (t + 1)) | (sbase & ((1u << t) - 1u));
   }
-  const uint32_t ss = swz(sbase);
+  const uint32_t ss = swz_t(sbase, a.swzt);
   // one tile per CTA: a loop over tiles would make the matrix entries
   // loop-invariant, and the compiler would then hold them in registers
   {
@@ -180,7 +216,7 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_apply_tile(float2* __res
     float2* const pt = psi + (base | a.roff[l0 >> a.C] | (l0 & ((1u << a.C) - 1u)));
     // bits 4..7 of the tile index 2t + 256c are bits 3..6 of t, so the
     // swizzle of both amplitudes of a chunk is the same for every c
-    const uint32_t fl = (tid >> 3) & 15u;
+    const uint32_t fl = a.swzt[(tid >> 3) & 15u];
     const uint32_t s0 = l0 ^ fl, s1 = (l0 + 1u) ^ fl;
     // load rows -> shared (coalesced 128-bit)
     float4 buf[NCH];
@@ -193,27 +229,26 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_apply_tile(float2* __res
     }
     __syncthreads();
     // one gather set per thread
-    float va[M], vb[M], vs[M];
+    float va[M];
+    float2 sb[M];    // (a + b, b) of member m
 #pragma unroll
     for (int m = 0; m < M; ++m) {
       const float2 v = sm[ss ^ a.smoff[m]];
       va[m] = v.x;
-      vb[m] = v.y;
-      vs[m] = v.x + v.y;
+      sb[m] = make_float2(v.x + v.y, v.y);
     }
-    // rows RU at a time: with a partial unroll the matrix entries come in
-    // through uniform constant loads (warp-uniform row index); an unbounded
-    // full unroll makes the compiler keep far more values live
+    // rows RU at a time: the matrix entries come in through uniform
+    // constant loads (warp-uniform row index)
 #pragma unroll RU
     for (int j = 0; j < M; ++j) {
-      float t = 0.f, r = 0.f, im = 0.f;
+      float2 tr = make_float2(0.f, 0.f);    // (sum c s, sum e b)
+      float im = 0.f;
 #pragma unroll
       for (int m = 0; m < M; ++m) {
-        t = fmaf(a.c[j][m], vs[m], t);
-        r = fmaf(a.e[j][m], vb[m], r);
+        tr = __ffma2_rn(a.ce[j][m], sb[m], tr);
         im = fmaf(a.f[j][m], va[m], im);
       }
-      sm[ss ^ a.smoff[j]] = make_float2(t - r, t + im);
+      sm[ss ^ a.smoff[j]] = make_float2(tr.x - tr.y, tr.x + im);
     }
     __syncthreads();
     // shared -> rows (coalesced 128-bit)
@@ -234,8 +269,7 @@ static cudaError_t launch_tile(float2* psi, int n, const uint32_t* targets, cons
   for (int j = 0; j < M; ++j)
     for (int m = 0; m < M; ++m) {
       const float re = U[j * M + m].x, im = U[j * M + m].y;
-      a.c[j][m] = re;
-      a.e[j][m] = re + im;
+      a.ce[j][m] = make_float2(re, re + im);
       a.f[j][m] = im - re;
     }
   // C = 7 + number of targets below C
@@ -259,11 +293,12 @@ static cudaError_t launch_tile(float2* psi, int n, const uint32_t* targets, cons
   }
   a.nh = nh;
   for (int b = 0; b < K; ++b) a.tins[b] = tpos[b];   // ascending: low targets, then C, C+1, ...
+  swizzle_table(tpos, K, a.swzt);
   for (int m = 0; m < M; ++m) {
     uint32_t o = 0;
     for (int b = 0; b < K; ++b)
       if ((m >> b) & 1) o |= 1u << tpos[b];
-    a.smoff[m] = o ^ ((o >> 4) & 15u);
+    a.smoff[m] = o ^ a.swzt[(o >> 4) & 15u];
   }
   for (int r = 0; r < M; ++r) {
     uint64_t o = 0;
@@ -278,7 +313,9 @@ static cudaError_t launch_tile(float2* psi, int n, const uint32_t* targets, cons
   }
   a.num_tiles = 1ull << (n - C - nh);
   if constexpr (K == 4)
-    k_apply_tile<4, 2, 8><<<static_cast<unsigned>(a.num_tiles), kTileThreads, 0, st>>>(psi, a);
+    k_apply_tile<4, 4, 8><<<static_cast<unsigned>(a.num_tiles), kTileThreads, 0, st>>>(psi, a);
+  else if constexpr (K == 5)
+    k_apply_tile<5, 2, 3><<<static_cast<unsigned>(a.num_tiles), kTileThreads, 0, st>>>(psi, a);
   else
     k_apply_tile<K><<<static_cast<unsigned>(a.num_tiles), kTileThreads, 0, st>>>(psi, a);
   return cudaGetLastError();

@@ -53,6 +53,27 @@ def test_apply_every_pattern(qt, orc, n, k):
         assert rel_l2(got, want) < KERNEL_L2, (qubits, rel_l2(got, want))
 
 
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_apply_every_low_target_set(qt, orc, k):
+    # The tile kernel picks its shared-memory swizzle from the targets below
+    # bit 8 of the tile index: every k-subset of the 12 lowest qubits of a
+    # 14-qubit state covers every such layout (C up to 11, high targets too).
+    import itertools
+    n = 14
+    rng = np.random.default_rng([14, k])
+    psi = random_state(n, k)
+    want_norm = np.linalg.norm(psi)
+    for qubits in itertools.combinations(range(12), k):
+        qubits = list(qubits)
+        U = qs.random_unitary(1 << k, rng)
+        d = to_device(psi)
+        qt.qt_state_apply(d.data_ptr(), n, qubits, U)
+        got = d.cpu().numpy()
+        want = orc.apply(psi.astype(np.complex128), qubits, U)
+        assert rel_l2(got, want) < KERNEL_L2, (qubits, rel_l2(got, want))
+        assert abs(np.linalg.norm(got) - want_norm) < 1e-5 * want_norm, qubits
+
+
 # split-TF32 on tensor cores: three TF32 products per term, so each product
 # carries ~3 * 2^-21 relative error and an output row sums 2^(k+1) of them;
 # 1e-5 relative L2 bounds one call
