@@ -11,10 +11,11 @@
 // width such that the row holds every "low" target plus 7 free bits; so a
 // row is at least 1 KB and every warp-wide 128-bit load or store of the
 // tile is fully coalesced whatever the target pattern.  The tile is staged
-// in shared memory with an XOR swizzle (8-byte slot ^= bits 4..7 of the
-// index) that keeps the strided gathers of low-target patterns free of bank
-// conflicts.  Each thread then gathers one set, multiplies, and scatters
-// it back; the tile is stored with the same coalesced pattern.
+// in shared memory with an XOR swizzle (8-byte slot ^= a per-launch linear
+// image of index bits 4..7) chosen so that the strided gathers of every
+// target pattern are free of bank conflicts.  Each thread then gathers one
+// set, multiplies, and scatters it back; the tile is stored with the same
+// coalesced pattern.
 //
 // The matrix is a __grid_constant__ kernel parameter: its entries reach the
 // FMAs through uniform registers loaded from the constant bank.  The complex
