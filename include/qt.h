@@ -50,7 +50,7 @@ typedef enum {
   QT_ERR_OUT_OF_MEMORY = -3, /* allocator or budget refused */
   QT_ERR_CUDA = -4,          /* CUDA runtime error (message names the call) */
   QT_ERR_TIMEOUT = -5,       /* a bounded device wait ran out */
-  QT_ERR_UNSUPPORTED = -6,   /* valid request outside this build's limits */
+  QT_ERR_UNSUPPORTED = -6,   /* valid request outside the library's limits */
   QT_ERR_INTERNAL = -7       /* device-side consistency check failed */
 } qt_status;
 
