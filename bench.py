@@ -271,7 +271,7 @@ def run_ours(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    apply_ms = apply_bytes = launches = passes = flushes = gate_ops = 0
+    apply_ms = apply_bytes = launches = passes = folded = flushes = gate_ops = 0
     ms_w = [0.0] * 8
     passes_w = [0] * 8
     for i in range(args.steps):
@@ -282,6 +282,7 @@ def run_ours(args):
         apply_bytes += s["apply_bytes"]
         launches += s["kernel_launches"]
         passes += s["fused_passes"]
+        folded += s["folded_pieces"]
         flushes += s["flushes"]
         for w in range(8):
             ms_w[w] += s["apply_ms_by_width"][w]
@@ -332,6 +333,7 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "num_qubits": N_QUBITS, "trajectories_per_step_per_gpu": T,
                    "fuse_k": FUSE_K, "mode": "delayed", "samples_per_traj": SAMPLES,
                    "fused_passes_per_traj": passes / (T * args.steps),
+                   "folded_pieces_per_traj": folded / (T * args.steps),
                    "flushes_per_traj": flushes / (T * args.steps),
                    "l2": "no flush: every pass streams the 8 GiB state (> 129 MB L2)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},

@@ -173,6 +173,9 @@ typedef struct {
                                  share one pass when a multi-gate pass groups them */
   uint64_t passes_by_width[8];  /* fused-gate passes by gate width 1..7; [0] = multi-gate passes */
   double apply_ms_by_width[8];  /* their device time (QT_FLAG_TIME_KERNELS, else 0) */
+  uint64_t folded_pieces;     /* leading fused gates folded into the initial product state
+                                 (each the first on its qubits; one write pass makes
+                                 U[:, 0] of all of them, for n >= 12); not in fused_passes */
 } qt_run_stats_t;
 qt_status qt_run_stats(const qt_run* r, qt_run_stats_t* out);
 

@@ -567,6 +567,60 @@ static unsigned stream_grid(uint64_t items) {
   return static_cast<unsigned>(g < cap ? (g ? g : 1) : cap);
 }
 
+// ---------------------------------------------------------------------------
+// Product-state preparation.  Fused gates that are the first to act on each
+// of their qubits, on disjoint qubits, take |0...0> to the tensor product of
+// their first columns (U |0> = U[:, 0]) with |0> on every other qubit.  With
+// the qubits split at m, each factor on the low or on the high side, the
+// amplitude is psi[x] = H[x >> m] * L[x mod 2^m]: the two tables are built
+// first (FP64 products of the factors, rounded once), then one write pass
+// fills the state, in place of the |0...0> pass and one pass per factor.
+// ---------------------------------------------------------------------------
+__global__ void k_fold_table(float2* __restrict__ out, uint32_t size, const __grid_constant__ FoldSpec s) {
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < size; e += stride) {
+    double re = 0.0, im = 0.0;
+    if (!(e & s.zmask)) {
+      re = 1.0;
+      for (int f = 0; f < s.nf; ++f) {
+        uint32_t j = 0;
+        for (int b = 0; b < s.w[f]; ++b) j |= ((e >> s.q[f][b]) & 1u) << b;
+        const float2 v = s.v[s.off[f] + j];
+        const double a = re * v.x - im * v.y;
+        im = re * v.y + im * v.x;
+        re = a;
+      }
+    }
+    out[e] = make_float2(static_cast<float>(re), static_cast<float>(im));
+  }
+}
+
+__global__ void __launch_bounds__(256) k_init_outer(float4* __restrict__ psi, const float2* __restrict__ tl,
+                                                    const float2* __restrict__ th, int m, uint64_t npairs) {
+  const uint64_t lmask = (1ull << m) - 1ull;
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < npairs; i += stride) {
+    const uint64_t x = 2ull * i;                  // even: both amplitudes share H[x >> m] (m >= 1)
+    const float4 l = *reinterpret_cast<const float4*>(tl + (x & lmask));
+    const float2 h = th[x >> m];
+    __stcs(psi + i, make_float4(h.x * l.x - h.y * l.y, h.x * l.y + h.y * l.x,
+                                h.x * l.z - h.y * l.w, h.x * l.w + h.y * l.z));
+  }
+}
+
+cudaError_t launch_init_product(float2* psi, int n, int m, const FoldSpec& lo, const FoldSpec& hi,
+                                float2* tables, cudaStream_t st) {
+  if (n < 2 || m < 1 || m >= n || m > kFoldTableBits || n - m > kFoldTableBits) return cudaErrorInvalidValue;
+  const uint32_t nl = 1u << m, nhi = 1u << (n - m);
+  float2* tl = tables;
+  float2* th = tables + nl;                      // nl even: th stays 16-byte aligned
+  k_fold_table<<<stream_grid(nl), 256, 0, st>>>(tl, nl, lo);
+  k_fold_table<<<stream_grid(nhi), 256, 0, st>>>(th, nhi, hi);
+  const uint64_t np = 1ull << (n - 1);
+  k_init_outer<<<stream_grid(np), 256, 0, st>>>(reinterpret_cast<float4*>(psi), tl, th, m, np);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_init_state(float2* psi, int n, cudaStream_t st) {
   if (n < 1) return cudaErrorInvalidValue;
   const uint64_t np = 1ull << (n - 1);

@@ -62,6 +62,23 @@ cudaError_t launch_apply_tc(float2* psi, int n, int k, const uint32_t* targets, 
 void real_embedding(int k, const float2* U, float* W);
 // |0...0>
 cudaError_t launch_init_state(float2* psi, int n, cudaStream_t st);
+// Product-state preparation: psi[x] = H[x >> m] * L[x mod 2^m], each table the
+// product of factor columns (U |0> of a fused gate on its own qubits) on the
+// qubits below m (L) or from m up (H); qubits no factor holds are |0>.
+constexpr int kFoldMax = 32;          // factors per table
+constexpr int kFoldVals = 1024;       // factor values per table
+constexpr int kFoldTableBits = 20;    // largest table: 2^20 entries
+struct FoldSpec {
+  float2 v[kFoldVals];                // factor columns, concatenated
+  uint16_t off[kFoldMax];             // offset of factor f's 2^w values in v
+  uint8_t w[kFoldMax];                // factor width (1..6)
+  uint8_t q[kFoldMax][6];             // qubit of index bit b of factor f, relative to the table
+  uint64_t zmask;                     // table bits that no factor holds (must be 0)
+  int nf;                             // factors
+};
+// tables: 2^m + 2^(n-m) complex64 of device scratch; 1 <= m, n - m <= 20
+cudaError_t launch_init_product(float2* psi, int n, int m, const FoldSpec& lo, const FoldSpec& hi,
+                                float2* tables, cudaStream_t st);
 // psi *= f
 cudaError_t launch_scale(float2* psi, int n, float f, cudaStream_t st);
 

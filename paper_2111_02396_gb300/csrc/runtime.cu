@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <bit>
 #include <cmath>
+#include <cstdlib>
 #include <deque>
 #include <cstring>
 #include <memory>
@@ -299,14 +300,15 @@ struct Controller {
   };
   std::deque<std::vector<float2>> owned;
 
-  // Apply ops [lo, hi) of the circuit.  choice[ch] is the operator of each
-  // channel; norm_scale[ch] > 0 marks a stage-2 choice applied as
-  // K_i * norm_scale (the Kraus form, normalized).
-  qt_status run_segment(float2* psi, uint32_t lo, uint32_t hi, const std::vector<int>& choice,
-                        const std::vector<double>& norm_scale) {
+  // The pieces of ops [lo, hi) of the circuit, in launch order.  choice[ch]
+  // is the operator of each channel; norm_scale[ch] > 0 marks a stage-2
+  // choice applied as K_i * norm_scale (the Kraus form, normalized).
+  // Composed pieces keep their matrices in `owned` until the next call.
+  void collect_pieces(uint32_t lo, uint32_t hi, const std::vector<int>& choice,
+                      const std::vector<double>& norm_scale, std::vector<Piece>& pieces) {
     std::vector<std::pair<uint32_t, const cd*>> seq;
     std::vector<std::vector<cd>> scaled;
-    std::vector<Piece> pieces;
+    pieces.clear();
     owned.clear();
     for (size_t g = 0; g < f.gates.size(); ++g) {
       const FusedGate& fg = f.gates[g];
@@ -353,7 +355,117 @@ struct Controller {
       to_f32(tmp, owned.back());
       pieces.push_back(Piece{targets, owned.back().data(), mask});
     }
+  }
+
+  // Apply ops [lo, hi) of the circuit.
+  qt_status run_segment(float2* psi, uint32_t lo, uint32_t hi, const std::vector<int>& choice,
+                        const std::vector<double>& norm_scale) {
+    std::vector<Piece> pieces;
+    collect_pieces(lo, hi, choice, norm_scale, pieces);
     return launch_pieces(psi, pieces);
+  }
+
+  // Product-state folding of the first segment.  A piece none of whose
+  // qubits an earlier piece of the segment touches acts on |0> of its own
+  // qubits and commutes with every piece before it, so it can move to the
+  // front and its output U[:, 0] becomes a factor of the initial product
+  // state.  The qubits are split at m; a factor must lie wholly below or
+  // wholly from m up.  m is chosen (tables of at most 2^20 entries) to fold
+  // the most pieces.  Returns m, or 0 when nothing folds.
+  static constexpr uint32_t kFoldMinQubits = 12;
+  DevBuf foldbuf;
+
+  int plan_fold(const std::vector<Piece>& pieces, std::vector<char>& fold) const {
+    const int n = static_cast<int>(R.n);
+    std::vector<size_t> first;
+    uint64_t touched = 0;
+    for (size_t i = 0; i < pieces.size(); ++i) {
+      if (!(pieces[i].full & touched)) first.push_back(i);
+      touched |= pieces[i].full;
+    }
+    if (first.empty()) return 0;
+    auto pick = [&](int m, std::vector<char>* mark) {
+      const uint64_t low = (1ull << m) - 1ull;
+      int side_n[2] = {0, 0}, side_v[2] = {0, 0}, cnt = 0;
+      for (size_t i : first) {
+        const uint64_t f = pieces[i].full;
+        const int side = (f & ~low) == 0 ? 0 : ((f & low) == 0 ? 1 : -1);
+        if (side < 0) continue;
+        const int d = 1 << pieces[i].targets.size();
+        if (side_n[side] >= kFoldMax || side_v[side] + d > kFoldVals) continue;
+        side_n[side]++;
+        side_v[side] += d;
+        cnt++;
+        if (mark) (*mark)[i] = 1;
+      }
+      return cnt;
+    };
+    const int mlo = std::max(1, n - kFoldTableBits), mhi = std::min(kFoldTableBits, n - 1);
+    int best_m = 0, best = 0;
+    for (int m = mlo; m <= mhi; ++m) {
+      const int cnt = pick(m, nullptr);
+      if (cnt > best || (cnt == best && cnt > 0 && std::abs(2 * m - n) < std::abs(2 * best_m - n))) {
+        best = cnt;
+        best_m = m;
+      }
+    }
+    if (best == 0) return 0;
+    fold.assign(pieces.size(), 0);
+    pick(best_m, &fold);
+    return best_m;
+  }
+
+  // Apply ops [0, hi) starting from |0...0>.
+  qt_status run_first_segment(float2* psi, uint32_t hi, const std::vector<int>& choice,
+                              const std::vector<double>& norm_scale) {
+    std::vector<Piece> pieces;
+    collect_pieces(0, hi, choice, norm_scale, pieces);
+    const int n = static_cast<int>(R.n);
+    std::vector<char> fold;
+    const int m = R.n >= kFoldMinQubits ? plan_fold(pieces, fold) : 0;
+    if (m == 0) {
+      QT_CUDA(launch_init_state(psi, n, R.st), "init kernel launch");
+      R.stats.kernel_launches++;
+      return launch_pieces(psi, pieces);
+    }
+    FoldSpec side[2];
+    uint64_t held[2] = {0, 0};
+    for (int k = 0; k < 2; ++k) {
+      std::memset(&side[k], 0, sizeof(FoldSpec));
+    }
+    std::vector<Piece> rest;
+    uint64_t folded = 0;
+    for (size_t i = 0; i < pieces.size(); ++i) {
+      if (!fold[i]) {
+        rest.push_back(pieces[i]);
+        continue;
+      }
+      const Piece& P = pieces[i];
+      const int k = (P.full >> m) == 0 ? 0 : 1;
+      const int base = k ? m : 0;
+      FoldSpec& S = side[k];
+      const int w = static_cast<int>(P.targets.size());
+      const int d = 1 << w;
+      const int f = S.nf++;
+      S.w[f] = static_cast<uint8_t>(w);
+      S.off[f] = static_cast<uint16_t>(f ? S.off[f - 1] + (1 << S.w[f - 1]) : 0);
+      for (int b = 0; b < w; ++b) {
+        S.q[f][b] = static_cast<uint8_t>(static_cast<int>(P.targets[b]) - base);
+        held[k] |= 1ull << S.q[f][b];
+      }
+      for (int j = 0; j < d; ++j) S.v[S.off[f] + j] = P.u[static_cast<size_t>(j) * d];   // column 0
+      folded++;
+    }
+    side[0].zmask = ((1ull << m) - 1ull) & ~held[0];
+    side[1].zmask = ((1ull << (n - m)) - 1ull) & ~held[1];
+    const size_t need = sizeof(float2) * ((1ull << m) + (1ull << (n - m)));
+    if (foldbuf.bytes < need && !foldbuf.alloc(need, R.st))
+      return set_error(QT_ERR_OUT_OF_MEMORY, "product-state tables");
+    QT_CUDA(launch_init_product(psi, n, m, side[0], side[1], foldbuf.as<float2>(), R.st),
+            "product-state kernel launch");
+    R.stats.kernel_launches += 3;
+    R.stats.folded_pieces += folded;
+    return launch_pieces(psi, rest);
   }
 
   // Launch the pieces of a segment in order.  With QT_FLAG_MULTI_GATE, consecutive
@@ -469,13 +581,11 @@ struct Controller {
         flush_ops.push_back(c.channel_op[ch]);
       }
     }
-    QT_CUDA(launch_init_state(psi, static_cast<int>(R.n), R.st), "init kernel launch");
-    R.stats.kernel_launches++;
     uint32_t lo = 0;
     const uint32_t nops = static_cast<uint32_t>(c.ops.size());
     for (size_t k = 0; k <= flush_ops.size(); ++k) {
       const uint32_t hi = k < flush_ops.size() ? flush_ops[k] : nops;
-      qt_status s = run_segment(psi, lo, hi, choice, scale);
+      qt_status s = k == 0 ? run_first_segment(psi, hi, choice, scale) : run_segment(psi, lo, hi, choice, scale);
       if (s != QT_OK) return s;
       if (k == flush_ops.size()) break;
       const uint32_t oi = flush_ops[k];

@@ -57,7 +57,8 @@ class qt_run_stats_t(C.Structure):
                 ("device_ms", C.c_double), ("apply_ms", C.c_double),
                 ("apply_bytes", C.c_uint64), ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64),
                 ("kernel_launches", C.c_uint64), ("fused_pieces", C.c_uint64),
-                ("passes_by_width", C.c_uint64 * 8), ("apply_ms_by_width", C.c_double * 8)]
+                ("passes_by_width", C.c_uint64 * 8), ("apply_ms_by_width", C.c_double * 8),
+                ("folded_pieces", C.c_uint64)]
 
 
 class qt_fused_info_t(C.Structure):
