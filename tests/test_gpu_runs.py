@@ -161,6 +161,18 @@ def test_noise_model_with_readout_errors(qt, orc, k):
     assert np.any(ref["stage"] == 2) and np.any(ref["kraus_idx"] == 2)   # three-operator stage 2 reached
 
 
+def test_product_state_start(qt, orc):
+    # From 12 qubits on, the fused gates that act first on their own qubits
+    # are folded into the initial product state (one write pass); branch
+    # records, states, samples and expectations still match the oracle.
+    circ = qs.config1_circuit(rows=3, cols=5)
+    run, _ = compare_run(qt, orc, circ, 4, k=4, mode=qt.QT_DELAYED, S=100, masks=[1, 0x7fff])
+    assert run.stats()["folded_pieces"] > 0
+    small = qs.config1_circuit(rows=2, cols=5)
+    r2, _ = compare_run(qt, orc, small, 2, k=4, mode=qt.QT_DELAYED, S=20)
+    assert r2.stats()["folded_pieces"] == 0
+
+
 def test_mixture_only_circuit_never_flushes(qt, orc):
     circ = qs.config3_circuit(rows=2, cols=5, depth=10, p=0.05)
     run, _ = compare_run(qt, orc, circ, 8, k=4, mode=qt.QT_DELAYED, S=50)
