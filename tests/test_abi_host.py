@@ -187,3 +187,47 @@ def test_fused_members_respect_qubit_order(qt):
             if q in last:
                 assert last[q] < i
             last[q] = i
+
+
+@pytest.mark.parametrize("case", ["grid3x4_k4", "chain10_k3", "random11_k2"])
+def test_first_touch_pieces_form_product_state(qt, orc, case):
+    """The identity behind the product-state start: the fused gates that act
+    first on each of their qubits (none of their qubits touched by an earlier
+    gate) take |0...0> to the tensor product of their first columns, with |0>
+    on every other qubit, and commute with every gate before them.  Folding
+    them first and then applying the other gates in order gives the state of
+    the plain sequence (FP64 oracle Alg. 1)."""
+    circ, n, k = {
+        "grid3x4_k4": (qs.config1_circuit(rows=3, cols=4, depth=8), 12, 4),
+        "chain10_k3": (qs.config0_circuit(), 10, 3),
+        "random11_k2": (qs.random_noisy_circuit(11, 120, 5, max_gate_qubits=2, channel_prob=0.3), 11, 2),
+    }[case]
+    f = qt.Fused(qt.Circuit.from_synth(circ), k)
+    gates = [f.gate(g) for g in range(f.info()["num_fused"])]
+    zero = np.zeros(1 << n, dtype=np.complex128)
+    zero[0] = 1.0
+    want = zero.copy()
+    for d in gates:
+        want = orc.apply(want, [int(q) for q in d["targets"]], d["matrix"])
+    touched, first = 0, []
+    for i, d in enumerate(gates):
+        mask = sum(1 << int(q) for q in d["targets"])
+        if not mask & touched:
+            first.append(i)
+        touched |= mask
+    assert first
+    x = np.arange(1 << n, dtype=np.int64)
+    held = 0
+    psi = np.ones(1 << n, dtype=np.complex128)
+    for i in first:
+        tg = [int(q) for q in gates[i]["targets"]]
+        j = np.zeros_like(x)
+        for b, q in enumerate(tg):
+            j |= ((x >> q) & 1) << b
+            held |= 1 << q
+        psi *= gates[i]["matrix"][j, 0]
+    psi[(x & ~held & ((1 << n) - 1)) != 0] = 0.0
+    for i, d in enumerate(gates):
+        if i not in first:
+            psi = orc.apply(psi, [int(q) for q in d["targets"]], d["matrix"])
+    np.testing.assert_allclose(psi, want, atol=1e-12)
