@@ -127,6 +127,15 @@ def dist_env():
     return rank, world, local
 
 
+def trajectory_ids(rank, world, step, per_rank):
+    """(first id, count) of the trajectories rank `rank` of `world` runs in step
+    `step`: the step's world * per_rank ids form one contiguous range, split into
+    contiguous per-rank parts, so the union over ranks of every step is the same
+    set of ids one process would run (trajectories are independent jobs, and the
+    counter-based draws depend only on the id)."""
+    return (step * world + rank) * per_rank, per_rank
+
+
 # ----------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle as it stands on a bounded sample
 # ----------------------------------------------------------------------------
@@ -246,7 +255,6 @@ def run_ours(args):
     qc = pkg.Circuit.from_synth(circ)
     fused = pkg.Fused(qc, FUSE_K)
     T = args.traj
-    base = rank * 10_000_000
 
     def barrier():
         if dist is not None:
@@ -254,7 +262,8 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     def step(i, flags=False):
-        return pkg.Run(fused, T, seed=0, first_traj=base + i * T, samples_per_traj=SAMPLES,
+        first, cnt = trajectory_ids(rank, world, i, T)
+        return pkg.Run(fused, cnt, seed=0, first_traj=first, samples_per_traj=SAMPLES,
                        time_kernels=flags, stream=sh)
 
     for i in range(args.warmup):
@@ -304,8 +313,8 @@ def run_ours(args):
     for i in range(args.steps):
         qc2 = pkg.Circuit.from_synth(circ)             # host op arrays -> library
         f2 = pkg.Fused(qc2, FUSE_K)
-        r = pkg.Run(f2, T, seed=0, first_traj=base + (args.warmup + i) * T, samples_per_traj=SAMPLES,
-                    stream=sh)
+        first, cnt = trajectory_ids(rank, world, args.warmup + i, T)
+        r = pkg.Run(f2, cnt, seed=0, first_traj=first, samples_per_traj=SAMPLES, stream=sh)
         smp = r.samples()                              # result on the host
         s = r.stats()
         h2d += s["h2d_bytes"]
@@ -354,7 +363,7 @@ def run_ours(args):
     line["amplitude_updates_per_s"] = world * passes * float(1 << N_QUBITS) / (ms / 1e3)
     line["gate_equivalent_updates_per_s"] = world * gate_ops * float(1 << N_QUBITS) / (ms / 1e3)
     if rank == 0 and world == 1 and not args.no_extras:
-        line["delayed_vs_eager"] = delayed_vs_eager(pkg, fused, sh, base + 9_000_000)
+        line["delayed_vs_eager"] = delayed_vs_eager(pkg, fused, sh, 9_000_000)
         line["bandwidth_probe_n32"] = bandwidth_probe(pkg, qs, sh)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, desc, _ = oracle_sample(target_s=args.ref_seconds)

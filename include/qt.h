@@ -134,7 +134,11 @@ typedef struct {
  * QT_ERR_OUT_OF_MEMORY, QT_ERR_CUDA, QT_ERR_UNSUPPORTED. */
 qt_status qt_run_trajectories(const qt_fused* f, const qt_run_params* p, qt_run** out);
 
-/* Bitstrings of the run: out[t * S + j] is sample j of trajectory t, bit k
+/* Bitstrings of the run (Sec. V.C: after each computation every qubit is
+ * measured, and the measured bitstrings are compared with the device's;
+ * Sec. II: measurement results of a Cirq circuit).  Each final state is
+ * measured in the computational basis, i.e. x is drawn with probability
+ * |psi_x|^2 / <psi|psi>: out[t * S + j] is sample j of trajectory t, bit k
  * = qubit k; the smallest x with u_j * C(2^n - 1) < C(x), C the cumulative
  * sum of |psi_x|^2 in index order (FP64), u_j = u01(seed, traj, 1, j).
  * S must equal the run's samples_per_traj, or, if the run kept its states,
@@ -142,7 +146,11 @@ qt_status qt_run_trajectories(const qt_fused* f, const qt_run_params* p, qt_run*
 qt_status qt_sample(qt_run* r, uint32_t samples_per_traj, uint64_t* out);
 
 /* Z-string expectations <psi| Z^{mask} |psi> / <psi|psi> of each final
- * state: out[t * num_terms + m].  The masks must equal the run's z_masks,
+ * state: out[t * num_terms + m].  These are the observables of Sec. V.C: the
+ * site densities P(q_j = 1) = (1 - <Z_j>) / 2 of the Fermi-Hubbard and
+ * non-interacting-fermion comparisons, and the Z-basis cost <C> of QAOA (a
+ * sum of Z-strings); averaged over r trajectories their Monte Carlo error
+ * falls as 1/sqrt(r) (Sec. III.E).  The masks must equal the run's z_masks,
  * or, if the run kept its states, be any masks (evaluated now). */
 qt_status qt_expectation(qt_run* r, uint32_t num_terms, const uint64_t* z_masks,
                          double* out);
@@ -176,6 +184,9 @@ typedef struct {
   uint64_t folded_pieces;     /* leading fused gates folded into the initial product state
                                  (each the first on its qubits; one write pass makes
                                  U[:, 0] of all of them, for n >= 12); not in fused_passes */
+  uint32_t fold_split;        /* qubit split m of the last product-state start (tables of
+                                 2^m and 2^(n-m) entries, each at most 2^20), 0 if none */
+  uint32_t pad;
 } qt_run_stats_t;
 qt_status qt_run_stats(const qt_run* r, qt_run_stats_t* out);
 
@@ -200,6 +211,11 @@ void qt_circuit_destroy(qt_circuit* c);
 void qt_fused_destroy(qt_fused* f);
 void qt_run_destroy(qt_run* r);
 const char* qt_last_error(void);
+
+/* Architecture the library's kernels were compiled for, as the CUDA runtime
+ * reports it for the current device (cudaFuncGetAttributes): binary_version
+ * 103 is sm_103a code (GB300); ptx_version 0 when no PTX is embedded. */
+qt_status qt_kernel_arch(int32_t* binary_version, int32_t* ptx_version);
 
 /* Introspection of the fused plan (host only, no GPU needed). */
 typedef struct {
@@ -228,11 +244,24 @@ qt_status qt_state_apply(void* state, uint32_t n, uint32_t q, const uint32_t* qu
  * 4^q complex, row-major.  P_i = tr(K_i^dag K_i rho) (Alg. 2 step 14). */
 qt_status qt_state_reduced_density(const void* state, uint32_t n, uint32_t q,
                                    const uint32_t* qubits, double* out, void* stream);
-/* S bitstrings from |psi|^2 with uniforms u01(seed, traj, 1, j); out host.
- * readout_error: NULL, or 2 per qubit as in qt_run_params (host, copied). */
+/* Measurement of every qubit (Sec. V.C) on a caller-owned state: S
+ * bitstrings x drawn with probability |psi_x|^2 / <psi|psi> (the cumulative
+ * rule of qt_sample) with uniforms u01(seed, traj, 1, j); out host, S
+ * entries.  readout_error: NULL, or 2 per qubit as in qt_run_params (the
+ * parallel readout errors of Sec. V.A; host, copied). */
 qt_status qt_state_sample(const void* state, uint32_t n, uint64_t seed, uint64_t traj,
                           uint32_t S, uint64_t* out, const double* readout_error, void* stream);
-/* Z-string expectations of the state (normalized by <psi|psi>); out host. */
+/* The cumulative distribution C(x) = sum_{y <= x} |psi_y|^2 that the
+ * measurement of Sec. V.C samples from (qt_state_sample, qt_sample), as the
+ * sampler itself forms it: FP32 squares and FP32 running sums inside runs of
+ * 1024 amplitudes, FP64 across runs.  out host, 2^n doubles (out[2^n - 1] is
+ * the total); n <= 28.  A sample x is the smallest x with u * C(2^n - 1) <
+ * C(x), so these values bound where a sample can land when u falls within
+ * rounding of a boundary. */
+qt_status qt_state_cdf(const void* state, uint32_t n, double* out, void* stream);
+/* Z-string expectations <psi| Z^{mask} |psi> / <psi|psi> of a caller-owned
+ * state (the Sec. V.C observables: site densities (1 - <Z_j>) / 2, QAOA
+ * Z-string costs); out host, num_terms doubles. */
 qt_status qt_state_expect_z(const void* state, uint32_t n, uint32_t num_terms,
                             const uint64_t* z_masks, double* out, void* stream);
 
@@ -364,9 +393,10 @@ void qt_server_destroy(qt_server* s);
  * scratch is one fixed array inside libqt.so: 1216 * 64 + 64 doubles
  * (608.5 KiB), which every GPU that loads the library holds until the process
  * exits; q must be <= 3 (larger requests are rejected with
- * QT_ERR_UNSUPPORTED and a message naming the limit).  The first call on a
- * device looks up that array's device address with the device current; make
- * that first call before any stream capture.  All calls share the array and
+ * QT_ERR_UNSUPPORTED and a message naming the limit).  Every call looks up
+ * that array's device address in the current context (so a device reset does
+ * not leave a stale address behind); the first call on a device may load the
+ * library's module there, so make that first call before any stream capture.  All calls share the array and
  * it keeps the last call's contents (nothing in it needs to start at zero),
  * so calls whose kernels overlap on the GPU -- different streams or host
  * threads -- race: order them. */

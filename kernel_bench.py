@@ -1,11 +1,13 @@
-"""Micro-benchmark of the fused-gate kernel (Alg. 1) and the read passes.
+"""Kernel micro-benchmark, a companion of bench.py: the fused-gate kernel
+(Alg. 1), the read passes, whole trajectories and the batched kernel, each
+timed alone.
 
 Times each kernel through the C ABI's state-level calls on a device state
 of 2^n complex64 amplitudes, with CUDA events on the launching stream after
 warm-up, and reports achieved bandwidth against the algorithmic bytes:
 16 * 2^n per fused-gate pass (read + write), 8 * 2^n per read pass.
 
-    python -m paper_2111_02396_gb300.kernel_bench --n 30 --k 4
+    python kernel_bench.py --n 30 --k 4
 """
 from __future__ import annotations
 
@@ -27,7 +29,7 @@ PATTERNS = {
 
 
 def main(argv=None):
-    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
     import torch
 
     import paper_2111_02396_gb300 as pkg

@@ -871,11 +871,11 @@ qt_status qt_batch_run(qt_batch* b, const qt_batch_params* p) {
   b->hrun[0] = p->seed;
   b->hrun[1] = p->first_traj;
   const size_t smem = (sizeof(float2) << bt::kSmemNMax) + sizeof(float2) * (1u << (2 * bt::kMaxW));
-  static std::once_flag once;
-  static cudaError_t attr = cudaSuccess;
-  std::call_once(once, [&] {
-    attr = cudaFuncSetAttribute(bt::k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  });
+  static PerDevice attr_set;
+  const cudaError_t attr = static_cast<cudaError_t>(attr_set.get([&] {
+    return static_cast<int>(
+        cudaFuncSetAttribute(bt::k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+  }));
   if (attr != cudaSuccess) return set_error(QT_ERR_CUDA, "qt_batch_run: smem attribute: %s", cudaGetErrorString(attr));
   const unsigned grid = static_cast<unsigned>(std::min<uint64_t>(sm_count(), b->num));
   struct Events {                   // the run's timing events, destroyed on every return

@@ -104,16 +104,14 @@ __global__ void __launch_bounds__(256) k_apply(float2* __restrict__ psi,
   }
 }
 
-static int g_sms = 0;
 int sm_count() {
-  static std::once_flag once;
-  std::call_once(once, [] {
-    int dev = 0;
+  static PerDevice sms;
+  return sms.get([] {
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_sms <= 0) g_sms = 1;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
   });
-  return g_sms;
 }
 
 
@@ -400,12 +398,11 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_apply_tile6(float2* __restr
 
 cudaError_t launch_apply6_fp32(float2* psi, int n, const uint32_t* targets, const float2* udev, cudaStream_t st) {
   if (n < 13) return cudaErrorInvalidValue;
-  static std::once_flag once;
-  static cudaError_t attr = cudaSuccess;
-  std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(k_apply_tile6, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(kTile6Smem));
-  });
+  static PerDevice attr_set;
+  const cudaError_t attr = static_cast<cudaError_t>(attr_set.get([] {
+    return static_cast<int>(cudaFuncSetAttribute(k_apply_tile6, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 static_cast<int>(kTile6Smem)));
+  }));
   if (attr != cudaSuccess) return attr;
   Tile6Args a;
   a.u = udev;
@@ -586,12 +583,12 @@ __global__ void __launch_bounds__(kGroupThreads, 2) k_apply_group(float2* __rest
 
 cudaError_t launch_apply_group(float2* psi, int n, int ng, const GroupPiece* pieces, cudaStream_t st) {
   if (ng < 1 || ng > kGroupMaxGates) return cudaErrorInvalidValue;
-  static std::once_flag once;
-  static cudaError_t attr = cudaSuccess;
-  std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(k_apply_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>((sizeof(float2) << 13) + sizeof(float) * kGroupMaxGates * 3 * 256));
-  });
+  static PerDevice attr_set;
+  const cudaError_t attr = static_cast<cudaError_t>(attr_set.get([] {
+    return static_cast<int>(cudaFuncSetAttribute(
+        k_apply_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        static_cast<int>((sizeof(float2) << 13) + sizeof(float) * kGroupMaxGates * 3 * 256)));
+  }));
   if (attr != cudaSuccess) return attr;
   GroupArgs a;
   // high qubits of the group (>= 7), ascending
@@ -657,11 +654,11 @@ static inline bool tile_fits(int n, int k) { return n >= 7 + k; }
 template <int K, bool PAIR>
 static cudaError_t launch_k(float2* psi, int n, const uint32_t* targets, const float2* U,
                             cudaStream_t st) {
-  static int occ = 0;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_apply<K, PAIR>, 256, 0);
-    if (occ <= 0) occ = 1;
+  static PerDevice occ_dev;
+  const int occ = occ_dev.get([] {
+    int v = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_apply<K, PAIR>, 256, 0);
+    return v > 0 ? v : 1;
   });
   ApplyArgs<K> a;
   constexpr int M = 1 << K;

@@ -478,11 +478,11 @@ static cudaError_t launch_tc_k(float2* psi, int n, const uint32_t* targets, cons
   constexpr int TILE_AMPS = tc::kTileSets * NM;
   constexpr int TBUF_AMPS = (NBUF * TILE_AMPS > 3 * TILE_AMPS / 2) ? NBUF * TILE_AMPS : 3 * TILE_AMPS / 2;
   const size_t smem = 2 * sizeof(float) * N * N + TBUF_AMPS * sizeof(float2) + 24 * sizeof(uint64_t) + 16;
-  static std::once_flag once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(once, [&] {
-    attr_err = cudaFuncSetAttribute(k_apply_tc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  });
+  static PerDevice attr_set;
+  const cudaError_t attr_err = static_cast<cudaError_t>(attr_set.get([&] {
+    return static_cast<int>(
+        cudaFuncSetAttribute(k_apply_tc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+  }));
   if (attr_err != cudaSuccess) return attr_err;
   TcArgs<K> a;
   // tile: 2^nh rows of 2^C contiguous amplitudes, C = 7 + targets below C

@@ -135,9 +135,8 @@ static cudaError_t rdm_q(const float2* psi, int n, const uint32_t* qubits, const
     a.offs[m] = o;
   }
   a.num_sets = 1ull << (n - Q);
-  static int grid = 0;
-  static std::once_flag once;
-  std::call_once(once, [] { grid = red_grid(k_rdm<Q>, ~0ull >> 1); });
+  static PerDevice grid_dev;
+  const int grid = grid_dev.get([] { return red_grid(k_rdm<Q>, ~0ull >> 1); });
   const uint64_t need = (a.num_sets + kRedThreads - 1) / kRedThreads;
   const int g = static_cast<int>(need < static_cast<uint64_t>(grid) ? need : grid);
   k_rdm<Q><<<g, kRedThreads, 0, st>>>(psi, a, scr.partial);
@@ -320,9 +319,8 @@ cudaError_t launch_expect(const float2* psi, int n, int nm, const uint64_t* mask
     }
     a.nm = nm;
     a.num_blocks = 1ull << (n - 9);
-    static int gridw = 0;
-    static std::once_flag oncew;
-    std::call_once(oncew, [] { gridw = red_grid(k_expect_wht, ~0ull >> 1); });
+    static PerDevice gridw_dev;
+    const int gridw = gridw_dev.get([] { return red_grid(k_expect_wht, ~0ull >> 1); });
     const uint64_t need = (a.num_blocks * 32 + kRedThreads - 1) / kRedThreads;
     const int g = static_cast<int>(need < static_cast<uint64_t>(gridw) ? need : gridw);
     k_expect_wht<<<g, kRedThreads, 0, st>>>(psi, a, scr.partial);
@@ -333,9 +331,8 @@ cudaError_t launch_expect(const float2* psi, int n, int nm, const uint64_t* mask
   for (int m = 0; m < kExpGroup; ++m) a.masks[m] = m < nm ? masks[m] : 0;
   a.nm = nm;
   a.num_pairs = 1ull << (n - 1);
-  static int grid = 0;
-  static std::once_flag once;
-  std::call_once(once, [] { grid = red_grid(k_expect, ~0ull >> 1); });
+  static PerDevice grid_dev;
+  const int grid = grid_dev.get([] { return red_grid(k_expect, ~0ull >> 1); });
   const uint64_t need = (a.num_pairs + kRedThreads - 1) / kRedThreads;
   const int g = static_cast<int>(need < static_cast<uint64_t>(grid) ? need : grid);
   k_expect<<<g, kRedThreads, 0, st>>>(psi, a, scr.partial);
@@ -522,9 +519,46 @@ __global__ void k_sample(const float2* __restrict__ psi, uint64_t namps, const f
   }
 }
 
-cudaError_t launch_sample(const float2* psi, int n, uint64_t seed, uint64_t traj, uint32_t S,
-                          uint64_t* out, const Scratch& scr, cudaStream_t st, const double* readout) {
-  if (n < 1) return cudaErrorInvalidValue;
+// C(x) for every x, exactly as k_sample compares against it: the FP64 table
+// up to the block, the FP64 lane scan up to the sub-block, and the FP32 run
+// inside the sub-block up to x (one warp per sub-block, same chunk arithmetic)
+__global__ void k_cdf_values(const float2* __restrict__ psi, uint64_t namps, const float* __restrict__ sub,
+                             uint64_t nsub, const double* __restrict__ cum, double* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warp = (static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = (static_cast<uint64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (uint64_t s = warp; s < nsub; s += nwarps) {
+    const uint64_t b = s >> 6;
+    double s0, s1;
+    block_lane_values(sub, nsub, b, lane, s0, s1);
+    const double incl = warp_incl_scan_d(s0 + s1, lane);
+    double excl = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (lane == 0) excl = 0.0;
+    const int L = static_cast<int>((s & 63) >> 1);
+    const double eL = __shfl_sync(0xffffffffu, excl, L);
+    const double s0L = __shfl_sync(0xffffffffu, s0, L);
+    const double base = (b ? cum[b - 1] : 0.0) + ((s & 1) ? eL + s0L : eL);
+    float run = 0.f;
+    for (int c = 0; c < (1 << (kCdfSubLog - kCdfChunkLog)); ++c) {
+      const uint64_t x0 = (s << kCdfSubLog) + (static_cast<uint64_t>(c) << kCdfChunkLog) + 2 * lane;
+      float w0, w1;
+      chunk_weights(psi, namps, x0, w0, w1);
+      const float inc = warp_incl_scan_f(w0 + w1, lane);
+      const float tot = __shfl_sync(0xffffffffu, inc, 31);
+      const float cend = run + inc;
+      const float cstart = cend - (w0 + w1);
+      if (x0 < namps) {
+        out[x0] = base + static_cast<double>(cstart + w0);
+        out[x0 + 1] = base + static_cast<double>(cend);
+      }
+      run += tot;
+    }
+  }
+}
+
+// the three table levels of the sampling CDF (sub-block runs, block scans,
+// FP64 table) into scr.cdf_sub / scr.cdf_cum
+static void build_cdf_tables(const float2* psi, int n, const Scratch& scr, cudaStream_t st) {
   const uint64_t namps = 1ull << n;
   const uint64_t nsub = cdf_num_sub(n), nblk = cdf_num_blk(n);
   const int threads = 256, wpb = threads / 32;
@@ -536,6 +570,28 @@ cudaError_t launch_sample(const float2* psi, int n, uint64_t seed, uint64_t traj
   if (gb > cap) gb = cap;
   k_cdf_blk<<<static_cast<unsigned>(gb), threads, 0, st>>>(scr.cdf_sub, nsub, nblk, scr.cdf_cum);
   k_cdf_scan<<<1, 1024, 0, st>>>(scr.cdf_cum, nblk);
+}
+
+cudaError_t launch_cdf_values(const float2* psi, int n, const Scratch& scr, double* out, cudaStream_t st) {
+  if (n < 1) return cudaErrorInvalidValue;
+  build_cdf_tables(psi, n, scr, st);
+  const uint64_t nsub = cdf_num_sub(n);
+  const int threads = 256, wpb = threads / 32;
+  uint64_t g = (nsub + wpb - 1) / wpb;
+  const uint64_t cap = static_cast<uint64_t>(sm_count()) * 8;
+  if (g > cap) g = cap;
+  k_cdf_values<<<static_cast<unsigned>(g), threads, 0, st>>>(psi, 1ull << n, scr.cdf_sub, nsub, scr.cdf_cum, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sample(const float2* psi, int n, uint64_t seed, uint64_t traj, uint32_t S,
+                          uint64_t* out, const Scratch& scr, cudaStream_t st, const double* readout) {
+  if (n < 1) return cudaErrorInvalidValue;
+  const uint64_t namps = 1ull << n;
+  const uint64_t nsub = cdf_num_sub(n), nblk = cdf_num_blk(n);
+  const int threads = 256, wpb = threads / 32;
+  const uint64_t cap = static_cast<uint64_t>(sm_count()) * 8;
+  build_cdf_tables(psi, n, scr, st);
   if (S > 0) {
     uint64_t gs = (S + wpb - 1) / wpb;
     if (gs > cap) gs = cap;
@@ -550,6 +606,15 @@ __global__ void k_init(float4* __restrict__ psi, uint64_t npairs) {
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
   for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < npairs; i += stride)
     psi[i] = make_float4(i == 0 ? 1.f : 0.f, 0.f, 0.f, 0.f);
+}
+
+cudaError_t kernel_arch(int* binary_version, int* ptx_version) {
+  cudaFuncAttributes a{};
+  const cudaError_t e = cudaFuncGetAttributes(&a, k_init);
+  if (e != cudaSuccess) return e;
+  *binary_version = a.binaryVersion;
+  *ptx_version = a.ptxVersion;
+  return cudaSuccess;
 }
 
 __global__ void k_scale(float4* __restrict__ psi, uint64_t npairs, float f) {

@@ -3,9 +3,33 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "qt.h"
 
 namespace qt {
+
+// A launch parameter that depends on the device (SM count, occupancy, a
+// kernel attribute set once): computed by f() the first time it is asked for
+// with a given device current, then reused for that device.  f() must be
+// idempotent (two threads may both compute it the first time).
+class PerDevice {
+ public:
+  template <typename F>
+  int get(F&& f) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return f();
+    const int v = vals_[dev].load(std::memory_order_acquire);
+    if (v != 0) return v - 1;
+    const int r = f();
+    vals_[dev].store(r + 1, std::memory_order_release);
+    return r;
+  }
+
+ private:
+  static constexpr int kMaxDevices = 64;
+  std::atomic<int> vals_[kMaxDevices] = {};
+};
 
 // ---- device scratch sizes -------------------------------------------------
 constexpr int kRedThreads = 256;          // threads of the reduction kernels
@@ -40,6 +64,8 @@ cudaError_t launch_expect(const float2* psi, int n, int nm, const uint64_t* mask
 // S samples of trajectory traj into out (device)
 cudaError_t launch_sample(const float2* psi, int n, uint64_t seed, uint64_t traj, uint32_t S,
                           uint64_t* out, const Scratch& scr, cudaStream_t st, const double* readout = nullptr);
+// C(x) of every x as the sampler forms it (2^n doubles into out, device)
+cudaError_t launch_cdf_values(const float2* psi, int n, const Scratch& scr, double* out, cudaStream_t st);
 // 6-qubit fused gate on CUDA cores (FP32), matrix 64x64 row-major in device memory, n >= 13
 cudaError_t launch_apply6_fp32(float2* psi, int n, const uint32_t* targets, const float2* udev, cudaStream_t st);
 // multi-gate pass: up to kGroupMaxGates fused gates (width <= 4, targets
@@ -87,5 +113,7 @@ cudaError_t launch_scale(float2* psi, int n, float f, cudaStream_t st);
 void rdm_unpack(int q, const double* r, double* rho_interleaved);
 
 int sm_count();
+// binaryVersion / ptxVersion of the library's kernels on the current device
+cudaError_t kernel_arch(int* binary_version, int* ptx_version);
 
 }  // namespace qt

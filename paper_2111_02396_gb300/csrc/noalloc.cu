@@ -21,13 +21,14 @@
 //     different host threads) race on it; callers must order them.
 //
 // The host-side name of a __device__ variable is not a device address, so
-// its address is looked up once per device with cudaGetSymbolAddress, with
-// that device current, the first time the entry point runs on it; that
-// first call should come before any stream capture.
+// the array's address is looked up with cudaGetSymbolAddress, with the
+// calling device current.  The lookup is repeated on every call rather than
+// cached: the address belongs to the context that loaded the module, and a
+// device reset (or a caller switching contexts) would leave a cached pointer
+// stale.  The lookup neither allocates nor enqueues work; the first call on a
+// device may load the library's module there, so that first call should come
+// before any stream capture.
 #include <cuda_runtime.h>
-
-#include <mutex>
-#include <vector>
 
 #include "kernels.h"
 #include "qt_internal.h"
@@ -38,25 +39,13 @@ constexpr size_t kNoAllocDoubles = static_cast<size_t>(kMaxRedBlocks) * 64 + 64;
 
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 
-static std::mutex g_noalloc_mu;
-static std::vector<double*> g_noalloc_addr;   // per device ordinal
-
 static qt_status noalloc_scratch(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess)
-    return set_error(QT_ERR_CUDA, "qt_state_reduced_density_noalloc: cudaGetDevice: %s", cudaGetErrorString(e));
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (g_noalloc_addr.size() <= static_cast<size_t>(dev)) g_noalloc_addr.resize(dev + 1, nullptr);
-  if (!g_noalloc_addr[dev]) {
-    double* p = nullptr;
-    e = cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      return set_error(QT_ERR_CUDA, "qt_state_reduced_density_noalloc: cudaGetSymbolAddress: %s",
-                       cudaGetErrorString(e));
-    g_noalloc_addr[dev] = p;
-  }
-  *out = g_noalloc_addr[dev];
+  double* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_noalloc_scratch);
+  if (e != cudaSuccess || !p)
+    return set_error(QT_ERR_CUDA, "qt_state_reduced_density_noalloc: cudaGetSymbolAddress: %s",
+                     cudaGetErrorString(e));
+  *out = p;
   return QT_OK;
 }
 

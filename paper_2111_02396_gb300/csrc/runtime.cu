@@ -465,6 +465,7 @@ struct Controller {
             "product-state kernel launch");
     R.stats.kernel_launches += 3;
     R.stats.folded_pieces += folded;
+    R.stats.fold_split = static_cast<uint32_t>(m);
     return launch_pieces(psi, rest);
   }
 
@@ -636,6 +637,16 @@ struct Controller {
 }  // namespace qt
 
 extern "C" {
+
+qt_status qt_kernel_arch(int32_t* binary_version, int32_t* ptx_version) {
+  clear_error();
+  if (!binary_version || !ptx_version) return set_error(QT_ERR_INVALID_ARG, "qt_kernel_arch: NULL argument");
+  int b = 0, p = 0;
+  QT_CUDA(kernel_arch(&b, &p), "qt_kernel_arch: cudaFuncGetAttributes");
+  *binary_version = b;
+  *ptx_version = p;
+  return QT_OK;
+}
 
 qt_status qt_set_allocator(qt_alloc_fn alloc, qt_free_fn free_fn, void* ctx) {
   clear_error();
@@ -973,6 +984,25 @@ qt_status qt_state_sample(const void* state, uint32_t n, uint64_t seed, uint64_t
                         ro.as<const double>()),
           "qt_state_sample");
   if (S) QT_CUDA(cudaMemcpyAsync(out, d.p, sizeof(uint64_t) * S, cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+  QT_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+  return QT_OK;
+}
+
+qt_status qt_state_cdf(const void* state, uint32_t n, double* out, void* stream) {
+  clear_error();
+  qt_status s = check_state(state, n, "qt_state_cdf");
+  if (s != QT_OK) return s;
+  if (n > 28) return set_error(QT_ERR_UNSUPPORTED, "qt_state_cdf: n=%u (at most 28: 2^n doubles go to the host)", n);
+  if (!out) return set_error(QT_ERR_INVALID_ARG, "qt_state_cdf: out is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ScratchBufs scr;
+  DevBuf d;
+  const size_t bytes = sizeof(double) << n;
+  if (!scr.alloc(static_cast<int>(n), st) || !d.alloc(bytes, st))
+    return set_error(QT_ERR_OUT_OF_MEMORY, "qt_state_cdf: scratch");
+  QT_CUDA(launch_cdf_values(static_cast<const float2*>(state), static_cast<int>(n), scr.s, d.as<double>(), st),
+          "qt_state_cdf");
+  QT_CUDA(cudaMemcpyAsync(out, d.p, bytes, cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
   QT_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
   return QT_OK;
 }

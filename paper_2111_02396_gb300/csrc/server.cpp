@@ -33,6 +33,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "kernels.h"
 #include "qt_internal.h"
 
 namespace qt {
@@ -78,6 +79,7 @@ using namespace qt;
 struct qt_server {
   qt_server_config cfg{};
   int device = 0;
+  uint32_t sms = 152;        // SMs of the device (sizes the batched form's arena)
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<uint64_t> queue;
@@ -100,13 +102,13 @@ struct qt_server {
 namespace qt {
 namespace {
 
-uint64_t footprint(const qt_server_config& c, uint32_t n, bool batched) {
+uint64_t footprint(uint32_t n, bool batched, uint32_t sms) {
   const uint64_t state = 8ull << n;
   // batched form: states <= 2^14 sit in shared memory; larger ones take one
-  // global slot per SM.  Plain loop: one resident state.  Plus scratch.
-  uint64_t b = batched ? (n > 14 ? state * 152 : 0) : state;
+  // global slot per SM (the arena qt_batch_run sizes by the SM count).  Plain
+  // loop: one resident state.  Plus scratch.
+  uint64_t b = batched ? (n > 14 ? state * sms : 0) : state;
   b += (16ull << 20) + (state >> 8);
-  (void)c;
   return b;
 }
 
@@ -289,6 +291,7 @@ qt_status qt_server_create(const qt_server_config* cfg, qt_server** out) {
   S->cfg = *cfg;
   if (!(cfg->flags & QT_SERVER_DRY_RUN)) {
     if (cudaGetDevice(&S->device) != cudaSuccess) return set_error(QT_ERR_CUDA, "qt_server_create: no CUDA device");
+    S->sms = static_cast<uint32_t>(sm_count());
   }
   S->workers.resize(cfg->max_slots);
   for (uint32_t w = 0; w < cfg->max_slots; ++w) {
@@ -313,7 +316,7 @@ qt_status qt_server_submit(qt_server* s, const qt_fused* f, const qt_server_requ
   q.r = *r;
   q.n = f->c->n;
   q.batched = use_batched(s->cfg, f, r->num_traj);
-  q.bytes = footprint(s->cfg, q.n, q.batched);
+  q.bytes = footprint(q.n, q.batched, s->sms);
   if (q.bytes > s->cfg.budget_bytes)
     return set_error(QT_ERR_OUT_OF_MEMORY, "qt_server_submit: footprint %llu bytes exceeds the budget %llu",
                      static_cast<unsigned long long>(q.bytes), static_cast<unsigned long long>(s->cfg.budget_bytes));

@@ -58,7 +58,7 @@ class qt_run_stats_t(C.Structure):
                 ("apply_bytes", C.c_uint64), ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64),
                 ("kernel_launches", C.c_uint64), ("fused_pieces", C.c_uint64),
                 ("passes_by_width", C.c_uint64 * 8), ("apply_ms_by_width", C.c_double * 8),
-                ("folded_pieces", C.c_uint64)]
+                ("folded_pieces", C.c_uint64), ("fold_split", C.c_uint32), ("pad", C.c_uint32)]
 
 
 class qt_fused_info_t(C.Structure):
@@ -120,9 +120,9 @@ EXPORTS = [
     "qt_circuit_create", "qt_fuse", "qt_run_trajectories", "qt_sample", "qt_expectation",
     "qt_run_kraus_indices", "qt_run_stats", "qt_run_state", "qt_run_norms", "qt_set_allocator",
     "qt_circuit_destroy", "qt_fused_destroy", "qt_run_destroy", "qt_last_error",
-    "qt_fused_info", "qt_fused_gate", "qt_channel_lower_bounds",
+    "qt_fused_info", "qt_fused_gate", "qt_channel_lower_bounds", "qt_kernel_arch",
     "qt_state_apply", "qt_state_reduced_density", "qt_state_sample", "qt_state_expect_z",
-    "qt_state_reduced_density_noalloc",
+    "qt_state_cdf", "qt_state_reduced_density_noalloc",
     "qt_fuse_many", "qt_batch_create", "qt_batch_run", "qt_batch_samples", "qt_batch_kraus_indices",
     "qt_batch_state", "qt_batch_stats", "qt_batch_destroy", "qt_batch_autotune",
     "qt_server_create", "qt_server_submit", "qt_server_poll", "qt_server_wait", "qt_server_cancel",
@@ -164,10 +164,12 @@ def load(build_if_missing: bool = True):
             "qt_fused_info": [P, P],
             "qt_fused_gate": [P, u32, P, P, P, P, C.c_size_t, P],
             "qt_channel_lower_bounds": [P, u32, P, C.c_size_t, P],
+            "qt_kernel_arch": [P, P],
             "qt_state_apply": [P, u32, u32, P, P, u32, P],
             "qt_state_reduced_density": [P, u32, u32, P, P, P],
             "qt_state_sample": [P, u32, u64, u64, u32, P, P, P],
             "qt_state_expect_z": [P, u32, u32, P, P, P],
+            "qt_state_cdf": [P, u32, P, P],
             "qt_state_reduced_density_noalloc": [P, u32, u32, P, P, P],
             "qt_fuse_many": [u32, P, u32, u32, P],
             "qt_batch_create": [u32, P, P],
@@ -461,6 +463,20 @@ def qt_state_sample(state_ptr, n, seed, traj, S, readout_error=None, stream=None
     _check(load().qt_state_sample(state_ptr, n, seed, traj, S, _ptr(out), _ptr(ro) if ro is not None else None,
                                   stream))
     return out[:S]
+
+
+def kernel_arch():
+    """(binaryVersion, ptxVersion) of the library's kernels on the current device."""
+    b, p = C.c_int32(0), C.c_int32(0)
+    _check(load().qt_kernel_arch(C.byref(b), C.byref(p)))
+    return b.value, p.value
+
+
+def qt_state_cdf(state_ptr, n, stream=None):
+    """The sampler's cumulative distribution C(x) of every x (2^n doubles)."""
+    out = np.zeros(1 << n, dtype=np.float64)
+    _check(load().qt_state_cdf(state_ptr, n, _ptr(out), stream))
+    return out
 
 
 def qt_state_expect_z(state_ptr, n, masks, stream=None):

@@ -28,6 +28,12 @@ def qt():
     return pkg
 
 
+def test_kernels_are_sm_103a_code(qt):
+    # the runtime reports the architecture of the loaded kernel image
+    binary, ptx = qt.kernel_arch()
+    assert binary == 103, (binary, ptx)
+
+
 def test_zero_trajectories_and_zero_samples(qt):
     circ = qs.config0_circuit()
     f = qt.Fused(qt.Circuit.from_synth(circ), 3)

@@ -8,12 +8,13 @@ any size:
   * a 30-qubit circuit made of six independent 5-qubit blocks (qubits
     interleaved across the index bits, fused to 4 qubits by the library):
     sampled amplitudes against the product of the six block states from
-    the oracle;
+    the oracle, and the samples of that state against the oracle's exact
+    per-block distributions (per-qubit marginals and a chi-square per block);
   * the 30-qubit 5x6 grid workload with damping: every stage-1 branch
     record equals the decision the oracle's own Philox draws and lower
-    bounds give; flushes happen exactly where stage 1 cannot decide; the
-    sampled bitstrings' per-qubit frequencies agree with <Z_j> of the same
-    final states.
+    bounds give; flushes happen exactly where stage 1 cannot decide; as a
+    consistency check of two different kernels, the sampled bitstrings'
+    per-qubit frequencies agree with <Z_j> of the same final states.
 """
 import numpy as np
 import pytest
@@ -102,6 +103,35 @@ def test_block_product_circuit_sampled_amplitudes(qt, orc):
     # relative L2 over the sample, scaled by the state's norm density
     err = np.linalg.norm(got - want) / np.linalg.norm(want)
     assert err < STATE_L2, err
+    # The sampled bitstrings against the oracle's exact distribution: the blocks
+    # are independent, so the 5 bits of block b in a sample follow |st_b|^2,
+    # and qubit q_j of block b is 1 with probability sum_{loc: bit j} |st_b[loc]|^2.
+    smp = run.samples()[0].astype(np.int64)
+    S = smp.size
+    for qs_b, st in states:
+        p = np.abs(st) ** 2
+        p /= p.sum()
+        loc = np.zeros(S, dtype=np.int64)
+        for j, q in enumerate(qs_b):
+            loc |= ((smp >> q) & 1) << j
+            p1 = p[(np.arange(p.size) >> j) & 1 == 1].sum()
+            freq = ((smp >> q) & 1).mean()
+            se = np.sqrt(max(p1 * (1 - p1), 1e-4) / S)
+            assert abs(freq - p1) < 5 * se, (q, freq, p1)
+        # chi-square over the 32 outcomes of the block (outcomes expected fewer
+        # than 5 times pooled into one bin)
+        cnt = np.bincount(loc, minlength=p.size).astype(np.float64)
+        exp = p * S
+        big = exp >= 5
+        obs_b = np.append(cnt[big], cnt[~big].sum())
+        exp_b = np.append(exp[big], exp[~big].sum())
+        keep = exp_b > 0
+        chi2 = float(np.sum((obs_b[keep] - exp_b[keep]) ** 2 / exp_b[keep]))
+        dof = int(keep.sum()) - 1
+        # 1e-6 tail of chi-square by the Wilson-Hilferty normal approximation
+        # (z = 4.75), so the 6 blocks fail together with probability < 1e-5
+        crit = dof * (1 - 2 / (9 * dof) + 4.75 * np.sqrt(2 / (9 * dof))) ** 3
+        assert chi2 < crit, (qs_b, chi2, crit)
 
 
 def test_grid30_branch_records_and_marginals(qt, orc):

@@ -29,11 +29,11 @@ def qt():
 
 
 def compare_run(qt, orc, circ, T, *, k, mode, seed=0, S=0, masks=(), check_states=True,
-                precision=0):
+                precision=0, grouping=False):
     qc = qt.Circuit.from_synth(circ)
     f = qt.Fused(qc, k)
     run = qt.Run(f, T, seed=seed, mode=mode, samples_per_traj=S, z_masks=masks,
-                 keep_states=check_states, precision=precision)
+                 keep_states=check_states, precision=precision, grouping=grouping)
     kr, st = run.kraus_indices()
     omode = orc.DELAYED if mode == qt.QT_DELAYED else orc.EAGER
     ref = orc.run_trajectories(circ, T, mode=omode, seed=seed, keep_states=True)
@@ -114,6 +114,24 @@ def test_grid_depolarizing_tf32x3(qt, orc, k):
     assert run.stats()["flushes"] == 0
 
 
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_multi_gate_passes_match_oracle(qt, orc, k):
+    """Multi-gate passes (several fused gates per pass over the state) against the
+    FP64 oracle: branch records, states, samples and expectations, on a 20-qubit
+    grid with flushes and on a 12-qubit random circuit with every channel kind."""
+    circ = qs.config1_circuit(rows=4, cols=5, depth=12, gamma=1e-2, lam=1e-2)
+    run, ref = compare_run(qt, orc, circ, 4, k=k, mode=qt.QT_DELAYED, seed=2, S=100,
+                           masks=[1, 1 << 19, 0xfffff], grouping=True)
+    st = run.stats()
+    assert st["passes_by_width"][0] > 0          # multi-gate passes ran
+    assert st["flushes"] == int(np.sum(ref["stage"] == 2)) and st["flushes"] > 0
+    circ = qs.random_noisy_circuit(12, 90, 321 + k, max_gate_qubits=2, noise=0.1,
+                                   channel_prob=0.4)
+    run, _ = compare_run(qt, orc, circ, 8, k=k, mode=qt.QT_DELAYED, seed=k, S=50,
+                         masks=[1, 0xfff], grouping=True)
+    assert run.stats()["passes_by_width"][0] > 0
+
+
 def test_multi_gate_passes_match_single_gate_passes(qt, orc):
     """Grouping fused gates into multi-gate passes changes only the pass count:
     same branch records, same states within float rounding, fewer passes."""
@@ -127,7 +145,6 @@ def test_multi_gate_passes_match_single_gate_passes(qt, orc):
     sa, sb = a.stats(), b.stats()
     assert sa["fused_pieces"] == sb["fused_pieces"]
     assert sa["fused_passes"] < sb["fused_passes"]
-    compare_run(qt, orc, circ, 4, k=4, mode=qt.QT_DELAYED, seed=2, S=100)
 
 
 @pytest.mark.parametrize("k", [3, 4])
@@ -171,6 +188,19 @@ def test_product_state_start(qt, orc):
     small = qs.config1_circuit(rows=2, cols=5)
     r2, _ = compare_run(qt, orc, small, 2, k=4, mode=qt.QT_DELAYED, S=20)
     assert r2.stats()["folded_pieces"] == 0
+
+
+@pytest.mark.parametrize("rows,cols", [(2, 11), (4, 6)])
+def test_product_state_start_large_split(qt, orc, rows, cols):
+    # At 22 and 24 qubits the split m of the product-state start must keep both
+    # tables within 2^20 entries (m >= n - 20), unlike the 15-qubit case where any
+    # split fits; one trajectory of each against the oracle.
+    circ = qs.config1_circuit(rows=rows, cols=cols, depth=10)
+    n = rows * cols
+    run, _ = compare_run(qt, orc, circ, 1, k=4, mode=qt.QT_DELAYED, S=200, masks=[1, (1 << n) - 1])
+    st = run.stats()
+    assert st["folded_pieces"] > 0
+    assert n - 20 <= st["fold_split"] <= 20
 
 
 def test_mixture_only_circuit_never_flushes(qt, orc):
