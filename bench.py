@@ -9,8 +9,15 @@ trajectories per GPU with the delayed inner-product algorithm (Alg. 2),
 100 bitstrings sampled from every final state.  Complex64 state (8 GiB,
 larger than L2, so no L2 flush is needed between steps).
 
-Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
-on a bounded sample of the same workload instead.
+Prints one JSON line (rank 0).  At N = 1 the line also carries the three
+systems forms of the metric, each measured in its own timed region with its
+own clock record: "batched" (8192 circuits of 8..18 qubits in one persistent
+launch, against the plain loop on the same GPU), "served" (a Poisson request
+stream with continuous batching, p50/p99 latency, against serving the same
+stream request by request) and "precision" (32-qubit circuits fused to 6
+qubits on tensor cores in split TF32, against FP32 CUDA-core comparators,
+error against the FP64 oracle at 26 qubits).  --impl reference times the
+FP64 CPU oracle on a bounded sample of the grid workload instead.
 """
 from __future__ import annotations
 
@@ -269,11 +276,7 @@ def run_ours(args):
     for i in range(args.warmup):
         step(i)
     # ---- device-timed loop (inputs resident: fused circuit built once) ----
-    uuid = None
-    try:
-        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
-    except Exception:  # noqa: BLE001 -- sample all GPUs instead
-        uuid = None
+    uuid = device_uuid(local)
     clocks = ClockSampler(uuid)
     barrier()
     clocks.start()
@@ -365,6 +368,11 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_extras:
         line["delayed_vs_eager"] = delayed_vs_eager(pkg, fused, sh, 9_000_000)
         line["bandwidth_probe_n32"] = bandwidth_probe(pkg, qs, sh)
+    if rank == 0 and world == 1 and not args.no_forms:
+        # the systems forms of the metric, each in its own timed region
+        line["batched"] = batched_form(uuid=uuid)
+        line["served"] = served_form(args.requests, args.slots, uuid)
+        line["precision"] = precision_form(uuid=uuid)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, desc, _ = oracle_sample(target_s=args.ref_seconds)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
@@ -376,26 +384,39 @@ def run_ours(args):
 
 
 # ----------------------------------------------------------------------------
-# batched form: 8192 small circuits in one persistent launch vs the plain loop
+# The three systems forms beside the plain loop.  Each form is a function that
+# returns its result object; the default run adds all three to the grid30 line
+# (each with the clocks sampled during its own GPU-timed region), and
+# --workload batch / serve / precision prints one of them as a line of its own.
 # ----------------------------------------------------------------------------
 BATCH_WORKLOAD = ("batch8192: 8192 circuits, n ~ U{8..18}, 1D chain, depth 40, sqrtX/sqrtY/sqrtW + CZ, "
                   "depolarizing 1e-3 then amplitude damping 1e-3 on every gate-qubit, one trajectory each, "
                   "100 samples per trajectory")
 
 
-def run_batch(args):
+def device_uuid(local=0):
+    import torch
+    try:
+        return "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:  # noqa: BLE001 -- sample all GPUs instead
+        return None
+
+
+def batched_form(steps=3, warmup=2, num=8192, plain_stride=32, uuid=None):
+    """Config 2: 8192 circuits of uneven size, one trajectory each, in one persistent
+    launch replayed as a CUDA graph, against the plain per-trajectory loop on the same
+    GPU (every plain_stride-th circuit, scaled) and the FP64 oracle."""
     import concurrent.futures as cf
 
     import numpy as np
     import torch
 
+    import oracle
     import paper_2111_02396_gb300 as pkg
     import qtsynth as qs
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
     pkg.load()
-    num = args.batch_size
+    oracle.build()
     t0 = time.perf_counter()
     ccs = [qs.config2_compact(i) for i in range(num)]
     t_gen = time.perf_counter() - t0
@@ -414,36 +435,38 @@ def run_batch(args):
     t0 = time.perf_counter()
     batch = pkg.Batch(fused)
     t_pack = time.perf_counter() - t0
-    base = rank * 10_000_000
-    for i in range(args.warmup):
-        batch.run(seed=0, first_traj=base + i * num, samples_per_traj=SAMPLES, use_graph=True,
-                  threads=best_t, stream=sh)
+    for i in range(warmup):
+        batch.run(seed=0, first_traj=i * num, samples_per_traj=SAMPLES, use_graph=True, threads=best_t, stream=sh)
+    clk = ClockSampler(uuid)
+    torch.cuda.synchronize()
+    clk.start()
     ms = []
-    for i in range(args.steps):
-        batch.run(seed=0, first_traj=base + (args.warmup + i) * num, samples_per_traj=SAMPLES,
-                  use_graph=True, threads=best_t, stream=sh)
+    for i in range(steps):
+        batch.run(seed=0, first_traj=(warmup + i) * num, samples_per_traj=SAMPLES, use_graph=True,
+                  threads=best_t, stream=sh)
         ms.append(batch.stats()["device_ms"])
+    clocks = clk.stop()
     batched = num / (statistics.median(ms) / 1e3)
     # plain per-trajectory loop on every stride-th circuit, scaled to the batch
-    stride = args.plain_stride
-    idx = list(range(0, num, stride))
+    idx = list(range(0, num, plain_stride))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i in idx:
-        pkg.Run(fused[i], 1, seed=0, first_traj=base + i, samples_per_traj=SAMPLES, stream=sh)
+        pkg.Run(fused[i], 1, seed=0, first_traj=i, samples_per_traj=SAMPLES, stream=sh)
     torch.cuda.synchronize()
-    plain_s = (time.perf_counter() - t0) * stride
-    plain = num / plain_s
-    # accuracy on a few trajectories against the FP64 oracle
-    import oracle
-    oracle.build()
-    small = [i for i in range(num) if ccs[i].num_qubits <= 12][:8]
-    sub = pkg.Batch([fused[i] for i in small]).run(seed=0, first_traj=0, samples_per_traj=0, keep_states=True)
+    plain = num / ((time.perf_counter() - t0) * plain_stride)
+    # accuracy against the FP64 oracle: trajectories of every size class
+    pick = []
+    for n in range(8, 19, 2):
+        pick += [i for i in range(num) if ccs[i].num_qubits == n][:2]
+    sub = pkg.Batch([fused[i] for i in pick]).run(seed=0, first_traj=0, samples_per_traj=0, keep_states=True,
+                                                  stream=sh)
     errs = []
-    for j, i in enumerate(small):
-        ref = oracle.run_trajectory(ccs[i].to_circuit(), oracle.DELAYED, seed=0, traj=j)["state"]
-        g = sub.state(j).astype(np.complex128)
-        errs.append(float(np.linalg.norm(g - ref) / np.linalg.norm(ref)))
+    for j, i in enumerate(pick):
+        ref = oracle.run_trajectory(ccs[i].to_circuit(), oracle.DELAYED, seed=0, traj=j)
+        if np.all(ref["margin"] > 1e-6):
+            g = sub.state(j).astype(np.complex128)
+            errs.append(float(np.linalg.norm(g - ref["state"]) / np.linalg.norm(ref["state"])))
     # the FP64 oracle on the host cores, on a spread sample of the batch
     stride_o = max(1, num // 32)
     sample_o = list(range(0, num, stride_o))
@@ -452,49 +475,55 @@ def run_batch(args):
         ref = oracle.run_trajectory(ccs[i].to_circuit(), oracle.DELAYED, seed=0, traj=i)
         oracle.sample(ref["state"], 0, i, SAMPLES)
     t_orc = time.perf_counter() - t0
-    cpu = {"value": len(sample_o) / t_orc, "unit": UNIT, "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
-           "sample": f"every {stride_o}th circuit ({len(sample_o)} trajectories with {SAMPLES} samples), FP64 "
-                     f"oracle, {t_orc:.1f} s"}
     st = batch.stats()
     amps = np.array([1 << c.num_qubits for c in ccs], dtype=np.float64)
     nf = np.array([f.info()["num_fused"] for f in fused], dtype=np.float64)
-    eff_bytes = float(np.sum(nf * amps * 16))
-    eff_gbs = eff_bytes / (statistics.median(ms) / 1e3) / 1e9
-    amp_updates = float(np.sum(nf * amps)) / (statistics.median(ms) / 1e3)
+    med_s = statistics.median(ms) / 1e3
+    eff_gbs = float(np.sum(nf * amps * 16)) / med_s / 1e9
     peak, peak_kind = measured_peaks()
-    line = {
-        "metric": METRIC, "value": batched, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": statistics.median(ms), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "form": "batched",
-        "config": {"workload": BATCH_WORKLOAD, "trajectories_per_step": num, "fuse_k": best_k,
-                   "threads_per_cta": best_t, "cuda_graph": True,
-                   "l2": "states of <= 2^14 amplitudes in shared memory, larger ones in per-CTA global "
-                         "slots (304 MB at n = 18, streamed from DRAM); inputs resident"},
-        "plain_loop": {"value": plain, "unit": UNIT,
-                       "sample": f"every {stride}th circuit ({len(idx)} trajectories), qt_run_trajectories "
-                                 f"one trajectory at a time on the same GPU, scaled by {stride}"},
+    return {
+        "workload": BATCH_WORKLOAD, "trajectories_per_run": num, "runs": steps, "warmup_runs": warmup,
+        "traj_per_s": batched, "ms_per_run": statistics.median(ms),
+        "fuse_k": best_k, "threads_per_cta": best_t, "cuda_graph": True,
+        "plain_loop": {"traj_per_s": plain,
+                       "sample": f"every {plain_stride}th circuit ({len(idx)} trajectories), qt_run_trajectories "
+                                 f"one trajectory at a time on the same GPU, scaled by {plain_stride}"},
         "speedup_vs_plain": batched / plain,
-        "amplitude_updates_per_s": amp_updates,
-        "cpu_baseline": cpu,
+        "amplitude_updates_per_s": float(np.sum(nf * amps)) / med_s,
         "effective_bandwidth": {"achieved": eff_gbs, "peak": peak, "unit": "GB/s", "frac": eff_gbs / peak,
                                 "peak_kind": peak_kind,
-                                "note": "algorithmic bytes (16 B x 2^n per fused pass) / kernel time; "
-                                        "states are shared-memory or L2 resident, so this is not an HBM figure"},
+                                "note": "algorithmic bytes (16 B x 2^n per fused pass) / kernel time; states of "
+                                        "<= 2^14 amplitudes live in shared memory, so this is not an HBM figure"},
         "l2_err_max": max(errs) if errs else None,
-        "l2_err_sample": f"{len(errs)} trajectories (n <= 12) against the FP64 oracle",
+        "l2_err_sample": f"{len(errs)} trajectories (2 of each n in 8, 10, .., 18) against the FP64 oracle",
         "autotune": {f"k{k}_t{t}": v for (k, t), v in table.items()},
+        "cpu_baseline": {"value": len(sample_o) / t_orc, "unit": UNIT, "cores": len(os.sched_getaffinity(0)),
+                         "kind": "oracle",
+                         "sample": f"every {stride_o}th circuit ({len(sample_o)} trajectories with {SAMPLES} "
+                                   f"samples), FP64 oracle, {t_orc:.1f} s"},
         "host_s": {"generate": t_gen, "create": t_create, "autotune": t_tune, "fuse": t_fuse, "pack": t_pack},
         "flushes_per_traj": st["flushes"] / num,
+        "clocks": clocks,
+    }
+
+
+def run_batch(args):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    b = batched_form(args.steps, args.warmup, args.batch_size, args.plain_stride, device_uuid(local))
+    line = {
+        "metric": METRIC, "value": b["traj_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": b["ms_per_run"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "form": "batched",
+        "config": {"workload": BATCH_WORKLOAD}, "batched": b,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
 
 
-# ----------------------------------------------------------------------------
-# serving form: a Poisson request stream, continuous batching vs request by request
-# ----------------------------------------------------------------------------
 SERVE_WORKLOAD = ("serve: requests with n ~ U{10..28}, depth ~ U{10..30}, chain or grid, depolarizing and "
                   "amplitude damping ~ logU[1e-4, 1e-2], trajectories ~ logU[1, 512], 100 samples per "
                   "trajectory, Poisson arrivals at 0.9x the plain loop's service rate, 150 GB HBM budget")
@@ -525,48 +554,48 @@ def serve_stream(pkg, fused, reqs, arrivals, *, slots, small_n_max, budget, keep
     batched = sum(srv.info(i)["batched"] for i in ids)
     kept = {k: srv.result(ids[k])[0] for k in keep}
     srv.close()
-    if keep:
-        return lat, done, st, batched, kept
-    return lat, done, st, batched
+    return lat, done, st, batched, kept
 
 
-def run_serve(args):
+def served_form(requests=160, slots=8, uuid=None):
+    """Config 4: the first `requests` requests of the seeded 2000-request stream, served
+    with continuous batching under a 150 GB budget, against the plain loop serving the
+    same stream request by request; Poisson arrivals at 0.9x the plain loop's service
+    rate, and a burst (all at t = 0) for the capacity of each form."""
     import concurrent.futures as cf
 
     import numpy as np
     import torch
 
+    import oracle
     import paper_2111_02396_gb300 as pkg
     import qtsynth as qs
 
-    torch.cuda.set_device(0)
     pkg.load()
-    R = args.requests
+    oracle.build()
+    R = requests
     reqs = qs.serving_requests(R, seed=0)
     with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 8) as ex:
         qcs = list(ex.map(lambda r: pkg.Circuit.from_compact(qs.request_compact(r)), reqs))
     fused = pkg.fuse_many(qcs, 4)
     budget = 150 * 10**9
-    # calibration: the plain loop serving the whole stream back to back gives
-    # its mean service time; arrivals come at 0.9x that service rate
-    lat, t_cal, _, _ = serve_stream(pkg, fused, reqs, [0.0] * R, slots=1, small_n_max=0, budget=budget)
-    cal = list(range(R))
-    mean_service = t_cal / R
-    rate = 0.9 / mean_service
+    clk = ClockSampler(uuid)
+    torch.cuda.synchronize()
+    clk.start()
+    # calibration = the plain loop's burst: the whole stream request by request
+    lat_c, t_cal, _, _, _ = serve_stream(pkg, fused, reqs, [0.0] * R, slots=1, small_n_max=0, budget=budget)
+    rate = 0.9 * R / t_cal
     rng = np.random.default_rng(1234)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, R)).tolist()
     arrivals = [a - arrivals[0] for a in arrivals]
     total_traj = sum(r["num_traj"] for r in reqs)
     # oracle parity on a seeded subsample: every 25th request with n <= 20, its first trajectory
     sub = [k for k in range(0, R, 25) if reqs[k]["n"] <= 20]
-    lat_s, t_s, st_s, nb, kept = serve_stream(pkg, fused, reqs, arrivals, slots=args.slots, small_n_max=20,
+    lat_s, t_s, st_s, nb, kept = serve_stream(pkg, fused, reqs, arrivals, slots=slots, small_n_max=20,
                                               budget=budget, keep=sub)
-    lat_p, t_p, st_p, _ = serve_stream(pkg, fused, reqs, arrivals, slots=1, small_n_max=0, budget=budget)
-    # burst variant: every request arrives at t = 0 (capacity of each form)
-    lat_b, t_b, _, _ = serve_stream(pkg, fused, reqs, [0.0] * R, slots=args.slots, small_n_max=20,
-                                    budget=budget)
-    import oracle
-    oracle.build()
+    lat_p, t_p, _, _, _ = serve_stream(pkg, fused, reqs, arrivals, slots=1, small_n_max=0, budget=budget)
+    lat_b, t_b, _, _, _ = serve_stream(pkg, fused, reqs, [0.0] * R, slots=slots, small_n_max=20, budget=budget)
+    clocks = clk.stop()
     compared = mismatched = 0
     for k in sub:
         r = reqs[k]
@@ -576,40 +605,50 @@ def run_serve(args):
         compared += int(ok.sum())
         mismatched += int(np.sum(kept[k][0][ok] != want[ok]))
     pct = lambda v, q: float(np.percentile(np.asarray(v), q))
-    line = {
-        "metric": METRIC, "value": total_traj / t_s, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
-        "ms_per_step": t_s * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic", "form": "served",
-        "config": {"workload": SERVE_WORKLOAD, "requests": R, "trajectories": total_traj, "slots": args.slots,
-                   "batched": "n <= 14, or n <= 20 with >= 64 trajectories", "arrival_rate_per_s": rate,
-                   "budget_bytes": budget},
-        "served": {"traj_per_s": total_traj / t_s, "p50_s": pct(lat_s, 50), "p99_s": pct(lat_s, 99),
-                   "makespan_s": t_s, "peak_inflight_bytes": st_s["peak_inflight_bytes"],
-                   "requests_batched": nb},
-        "plain_request_by_request": {"traj_per_s": total_traj / t_p, "p50_s": pct(lat_p, 50),
-                                     "p99_s": pct(lat_p, 99), "makespan_s": t_p},
-        "speedup_vs_plain": t_p / t_s,
+    return {
+        "workload": SERVE_WORKLOAD, "requests": R, "of_stream": 2000, "trajectories": total_traj,
+        "slots": slots, "arrival_rate_per_s": rate, "budget_bytes": budget,
+        "batched_requests": "n <= 14, or n <= 20 with >= 64 trajectories",
+        "poisson": {"served": {"traj_per_s": total_traj / t_s, "p50_s": pct(lat_s, 50), "p99_s": pct(lat_s, 99),
+                               "makespan_s": t_s, "peak_inflight_bytes": st_s["peak_inflight_bytes"],
+                               "requests_batched": nb},
+                    "plain_request_by_request": {"traj_per_s": total_traj / t_p, "p50_s": pct(lat_p, 50),
+                                                 "p99_s": pct(lat_p, 99), "makespan_s": t_p}},
         "burst": {"served_traj_per_s": total_traj / t_b, "plain_traj_per_s": total_traj / t_cal,
                   "served_p50_s": pct(lat_b, 50), "served_p99_s": pct(lat_b, 99),
-                  "plain_p50_s": pct(lat, 50), "plain_p99_s": pct(lat, 99),
+                  "plain_p50_s": pct(lat_c, 50), "plain_p99_s": pct(lat_c, 99),
                   "capacity_ratio": t_cal / t_b},
-        "calibration": {"requests": len(cal), "mean_service_s": mean_service},
         "parity": {"requests": sub, "samples_compared": compared, "sample_mismatches": mismatched,
                    "note": "first trajectory of every 25th request with n <= 20 against the FP64 oracle; "
                            "samples whose CDF margin is <= 1e-6 are ties and not compared"},
+        "clocks": clocks,
+    }
+
+
+def run_serve(args):
+    import torch
+
+    torch.cuda.set_device(0)
+    f = served_form(args.requests, args.slots, device_uuid(0))
+    line = {
+        "metric": METRIC, "value": f["poisson"]["served"]["traj_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1,
+        "warmup": 0, "ms_per_step": f["poisson"]["served"]["makespan_s"] * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "form": "served",
+        "config": {"workload": SERVE_WORKLOAD, "requests": args.requests}, "served": f,
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
-# ----------------------------------------------------------------------------
-# precision form: 6-qubit fused gates, split-TF32 tensor cores vs FP32 CUDA cores
-# ----------------------------------------------------------------------------
 PRECISION_WORKLOAD = ("precision: 4x8 grid (n=32) [2x13 grid (n=26) for the error], depth 24, "
-                      "sqrtX/sqrtY/sqrtW + CZ, depolarizing 1e-3 on every gate-qubit, fused k=6")
+                      "sqrtX/sqrtY/sqrtW + CZ, depolarizing 1e-3 on every gate-qubit")
 
 
-def run_precision(args):
+def precision_form(traj=32, traj_fp32_k6=4, oracle_traj=2, uuid=None):
+    """Config 3: 6-qubit fused gates on tensor cores in split TF32 against two FP32
+    CUDA-core comparators: the same k = 6 plan (k_apply_tile6) and the same circuit
+    fused to k = 4 (k_apply_tile<4>, the plain loop's kernel).  Throughput and norm
+    drift at n = 32, error against the FP64 oracle at n = 26."""
     import numpy as np
     import torch
 
@@ -617,47 +656,40 @@ def run_precision(args):
     import paper_2111_02396_gb300 as pkg
     import qtsynth as qs
 
-    torch.cuda.set_device(0)
     pkg.load()
     oracle.build()
     sh = torch.cuda.current_stream().cuda_stream
-    out = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic", "form": "precision",
-           "config": {"workload": PRECISION_WORKLOAD, "fuse_k": 6}}
+    forms = (("tf32x3_k6", pkg.QT_TF32X3, 6, traj), ("fp32_k6", pkg.QT_FP32, 6, traj_fp32_k6),
+             ("fp32_k4", pkg.QT_FP32, 4, traj))
     # error against the FP64 oracle at n = 26
     c26 = qs.config3_circuit(rows=2, cols=13, depth=24)
-    f26 = pkg.Fused(pkg.Circuit.from_synth(c26), 6)
-    T26 = 4
     t0 = time.perf_counter()
-    refs = [oracle.run_trajectory(c26, oracle.DELAYED, seed=0, traj=t)["state"] for t in range(T26)]
+    refs = [oracle.run_trajectory(c26, oracle.DELAYED, seed=0, traj=t)["state"] for t in range(oracle_traj)]
     t_orc = time.perf_counter() - t0
     errs = {}
-    for name, prec in (("tf32x3", pkg.QT_TF32X3), ("fp32", pkg.QT_FP32)):
-        r = pkg.Run(f26, T26, seed=0, precision=prec, keep_states=True, stream=sh)
+    for name, prec, k, _ in forms:
+        r = pkg.Run(pkg.Fused(pkg.Circuit.from_synth(c26), k), oracle_traj, seed=0, precision=prec,
+                    keep_states=True, stream=sh)
         l2, fid = [], []
-        for t in range(T26):
+        for t in range(oracle_traj):
             g = r.state(t).astype(np.complex128)
             ref = refs[t]
             l2.append(float(np.linalg.norm(g - ref) / np.linalg.norm(ref)))
             fid.append(float(abs(np.vdot(ref, g)) ** 2 / (np.vdot(g, g).real * np.vdot(ref, ref).real)))
-        errs[name] = {"trajectories": T26, "rel_l2_max": max(l2), "rel_l2_mean": float(np.mean(l2)),
-                      "fidelity_min": min(fid)}
-    out["error_n26"] = errs
-    out["oracle_n26_s"] = t_orc
-    out["cpu_baseline"] = {"value": T26 / t_orc, "unit": "trajectories/s (n = 26)",
-                           "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
-                           "sample": f"{T26} trajectories of the 26-qubit error workload (FP64, unfused)"}
+        errs[name] = {"trajectories": oracle_traj, "rel_l2_max": max(l2), "fidelity_min": min(fid)}
     # throughput and norm drift at n = 32
     c32 = qs.config3_circuit()
-    f32 = pkg.Fused(pkg.Circuit.from_synth(c32), 6)
     res = {}
-    for name, prec in (("tf32x3", pkg.QT_TF32X3), ("fp32", pkg.QT_FP32)):
-        # the 32 trajectories of the workload on tensor cores; the slower FP32 comparator on a few
-        T = args.traj_precision if prec == pkg.QT_TF32X3 else min(args.traj_precision, 4)
-        pkg.Run(f32, 1, seed=0, first_traj=10_000, precision=prec, stream=sh)     # warm-up
+    clk = ClockSampler(uuid)
+    for name, prec, k, T in forms:
+        f = pkg.Fused(pkg.Circuit.from_synth(c32), k)
+        pkg.Run(f, 1, seed=0, first_traj=10_000, precision=prec, stream=sh)     # warm-up
+        if name == "tf32x3_k6":
+            torch.cuda.synchronize()
+            clk.start()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        r = pkg.Run(f32, T, seed=0, precision=prec, samples_per_traj=SAMPLES, time_kernels=True, stream=sh)
+        r = pkg.Run(f, T, seed=0, precision=prec, samples_per_traj=SAMPLES, time_kernels=True, stream=sh)
         e1.record()
         torch.cuda.synchronize()
         st = r.stats()
@@ -666,16 +698,36 @@ def run_precision(args):
                      "amplitude_updates_per_s": st["fused_passes"] * float(1 << 32) / (ms / 1e3),
                      "apply_gbs": st["apply_bytes"] / (st["apply_ms"] / 1e3) / 1e9,
                      "fused_passes_per_traj": st["fused_passes"] / T,
-                     "norm_drift_max": float(np.max(np.abs(r.norms() - 1.0)))}
-    out["n32"] = res
-    out["value"] = res["tf32x3"]["traj_per_s"]
-    out["steps"], out["warmup"] = 1, 1
-    out["ms_per_step"] = 1e3 * res["tf32x3"]["trajectories"] / res["tf32x3"]["traj_per_s"]
+                     "norm_drift_max": float(np.max(np.abs(r.norms() - 1.0))),
+                     "error_n26": errs[name]}
+    clocks = clk.stop()
     peak, kind = measured_peaks()
-    out["roofline"] = {"bound": "hbm", "kernel": "k_apply_tc<6> (split-TF32 tcgen05)",
-                       "achieved": res["tf32x3"]["apply_gbs"], "peak": peak, "unit": "GB/s",
-                       "frac": res["tf32x3"]["apply_gbs"] / peak, "peak_kind": kind}
-    print(json.dumps(out), flush=True)
+    tc = res["tf32x3_k6"]
+    best_fp32 = max(("fp32_k6", "fp32_k4"), key=lambda nm: res[nm]["traj_per_s"])
+    return {
+        "workload": PRECISION_WORKLOAD, "n32": res, "traj_per_s": tc["traj_per_s"],
+        "tf32x3_over_best_fp32": tc["traj_per_s"] / res[best_fp32]["traj_per_s"], "best_fp32": best_fp32,
+        "roofline": {"bound": "hbm", "kernel": "k_apply_tc<6> (split-TF32 tcgen05)", "achieved": tc["apply_gbs"],
+                     "peak": peak, "unit": "GB/s", "frac": tc["apply_gbs"] / peak, "peak_kind": kind},
+        "cpu_baseline": {"value": oracle_traj / t_orc, "unit": "trajectories/s (n = 26)",
+                         "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                         "sample": f"{oracle_traj} trajectories of the 26-qubit error workload (FP64, unfused), "
+                                   f"{t_orc:.1f} s"},
+        "clocks": clocks,
+    }
+
+
+def run_precision(args):
+    import torch
+
+    torch.cuda.set_device(0)
+    f = precision_form(args.traj_precision, min(args.traj_precision, 4), 4, device_uuid(0))
+    line = {"metric": METRIC, "value": f["traj_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": 1e3 * f["n32"]["tf32x3_k6"]["trajectories"] / f["traj_per_s"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "form": "precision", "config": {"workload": PRECISION_WORKLOAD},
+            "precision": f, "roofline": f["roofline"]}
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -819,7 +871,9 @@ def main():
                     default="grid30",
                     help="grid30: the plain loop at scale (default); batch: the batched form; "
                          "serve: the serving loop")
-    ap.add_argument("--requests", type=int, default=120, help="serve: requests of the stream")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="grid30: skip the batched, served and precision forms")
+    ap.add_argument("--requests", type=int, default=160, help="serve: requests of the stream")
     ap.add_argument("--slots", type=int, default=8, help="serve: concurrent requests")
     ap.add_argument("--traj-precision", type=int, default=32, help="precision: trajectories at n=32")
     ap.add_argument("--batch-size", type=int, default=8192)

@@ -59,6 +59,7 @@ typedef enum { QT_DELAYED = 0, QT_EAGER = 1 } qt_mode;
 typedef enum { QT_FP32 = 0, QT_TF32X3 = 1 } qt_precision;
 #define QT_FLAG_TIME_KERNELS 1u
 #define QT_FLAG_MULTI_GATE 2u    /* group fused gates into multi-gate passes (opt-in) */
+#define QT_FLAG_SHARE_PREFIX 4u  /* share the default-choice prefix between trajectories (opt-in) */
 
 #define QT_MAX_QUBITS 34      /* largest state: 2^34 complex64 = 128 GiB */
 #define QT_MAX_OP_QUBITS 6    /* widest gate or channel */
@@ -110,7 +111,16 @@ typedef struct {
   const uint64_t* z_masks;     /* num_z_masks masks (copied) */
   uint32_t keep_states;        /* 1: keep every final state on the device */
   uint32_t flags;              /* QT_FLAG_TIME_KERNELS: time each fused-gate pass;
-                                  QT_FLAG_MULTI_GATE: several fused gates per pass */
+                                  QT_FLAG_MULTI_GATE: several fused gates per pass;
+                                  QT_FLAG_SHARE_PREFIX: delayed mode only -- stage 1 fixes, before
+                                  any kernel runs, each trajectory's first channel whose draw
+                                  leaves the default operator; the operators before it are the
+                                  same for every trajectory, so one shared state advances along
+                                  that default path and each trajectory copies it at its own
+                                  point (16 * 2^n bytes) and runs only the rest.  Same draws,
+                                  branch records and samples; states equal up to FP32 rounding
+                                  (fused pieces are split at the copy points).  Needs one more
+                                  state buffer. */
   void* stream;                /* cudaStream_t (0 = legacy default stream) */
   uint64_t timeout_ns;         /* bound on any device wait (0 = 10 s) */
   const double* readout_error; /* NULL, or readout errors of the samples (Sec. V.A, parallel
@@ -187,6 +197,9 @@ typedef struct {
   uint32_t fold_split;        /* qubit split m of the last product-state start (tables of
                                  2^m and 2^(n-m) entries, each at most 2^20), 0 if none */
   uint32_t pad;
+  uint64_t prefix_copies;     /* QT_FLAG_SHARE_PREFIX: copies of the shared state */
+  uint64_t prefix_ops;        /* QT_FLAG_SHARE_PREFIX: operations the trajectories took from the
+                                 shared state (summed over trajectories) */
 } qt_run_stats_t;
 qt_status qt_run_stats(const qt_run* r, qt_run_stats_t* out);
 

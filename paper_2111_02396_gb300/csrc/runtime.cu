@@ -559,34 +559,60 @@ struct Controller {
     return QT_OK;
   }
 
-  qt_status trajectory(uint32_t t, float2* psi) {
+  // Stage 1 of every channel of a trajectory (Alg. 2): the operator each
+  // channel's draw selects from the lower bounds alone, or a flush point where
+  // it does not; `diverge` is the first channel whose draw does not keep the
+  // channel's default operator in stage 1 (nch if every channel does).
+  struct Stage1 {
+    std::vector<int> choice;
+    std::vector<double> rdraw;
+    std::vector<uint32_t> flush_ops;
+    uint32_t diverge = 0;
+  };
+
+  void stage1(uint32_t t, Stage1& s1) {
     const uint64_t traj = R.p.first_traj + t;
     const uint32_t nch = R.nch;
-    std::vector<int> choice(nch, 0);
-    std::vector<double> scale(nch, 0.0);
-    std::vector<double> rdraw(nch);
-    std::vector<uint32_t> flush_ops;
+    s1.choice.assign(nch, 0);
+    s1.rdraw.resize(nch);
+    s1.flush_ops.clear();
+    s1.diverge = nch;
     int32_t* kr = R.kraus.data() + static_cast<size_t>(t) * nch;
     int32_t* sg = R.stage.data() + static_cast<size_t>(t) * nch;
     for (uint32_t ch = 0; ch < nch; ++ch) {
       const Op& op = c.ops[c.channel_op[ch]];
-      rdraw[ch] = uniform01(R.p.seed, traj, kStreamChannel, ch);
+      s1.rdraw[ch] = uniform01(R.p.seed, traj, kStreamChannel, ch);
       int st = 0;
-      const int ci = (R.p.mode == QT_DELAYED) ? decide(op, rdraw[ch], nullptr, 1.0, &st) : -1;
+      const int ci = (R.p.mode == QT_DELAYED) ? decide(op, s1.rdraw[ch], nullptr, 1.0, &st) : -1;
       if (ci >= 0) {
-        choice[ch] = ci;
+        s1.choice[ch] = ci;
         kr[ch] = ci;
         sg[ch] = 1;
       } else {
-        choice[ch] = op.def;
-        flush_ops.push_back(c.channel_op[ch]);
+        s1.choice[ch] = op.def;
+        s1.flush_ops.push_back(c.channel_op[ch]);
       }
+      if (ci != op.def && s1.diverge == nch) s1.diverge = ch;
     }
-    uint32_t lo = 0;
+  }
+
+  // Ops [start, end) of trajectory t on psi, which already holds ops [0, start)
+  // with every channel among them on its default operator (start = 0: psi is
+  // prepared from |0...0>).  Every flush point of the trajectory is at or
+  // after start.
+  qt_status run_from(uint32_t t, float2* psi, const Stage1& s1, uint32_t start) {
+    const uint32_t nch = R.nch;
+    std::vector<int> choice = s1.choice;
+    std::vector<double> scale(nch, 0.0);
+    int32_t* kr = R.kraus.data() + static_cast<size_t>(t) * nch;
+    int32_t* sg = R.stage.data() + static_cast<size_t>(t) * nch;
+    const std::vector<uint32_t>& flush_ops = s1.flush_ops;
+    uint32_t lo = start;
     const uint32_t nops = static_cast<uint32_t>(c.ops.size());
     for (size_t k = 0; k <= flush_ops.size(); ++k) {
       const uint32_t hi = k < flush_ops.size() ? flush_ops[k] : nops;
-      qt_status s = k == 0 ? run_first_segment(psi, hi, choice, scale) : run_segment(psi, lo, hi, choice, scale);
+      qt_status s = (k == 0 && start == 0) ? run_first_segment(psi, hi, choice, scale)
+                                           : run_segment(psi, lo, hi, choice, scale);
       if (s != QT_OK) return s;
       if (k == flush_ops.size()) break;
       const uint32_t oi = flush_ops[k];
@@ -595,13 +621,87 @@ struct Controller {
       s = probabilities(psi, oi, N, P);
       if (s != QT_OK) return s;
       int st = 2;
-      const int ci = decide(op, rdraw[op.channel], P, N, &st);
+      const int ci = decide(op, s1.rdraw[op.channel], P, N, &st);
       choice[op.channel] = ci;
       scale[op.channel] = 1.0 / std::sqrt(P[ci] > 0.0 ? P[ci] : 1.0);
       kr[op.channel] = ci;
       sg[op.channel] = st;
       R.stats.flushes += (st == 2);
       lo = oi;
+    }
+    return QT_OK;
+  }
+
+  qt_status trajectory(uint32_t t, float2* psi) {
+    Stage1 s1;
+    stage1(t, s1);
+    return run_from(t, psi, s1, 0);
+  }
+
+  qt_status finish_trajectory(uint32_t t, const float2* psi, uint64_t* d_samples) {
+    qt_status s = measure(t, psi, d_samples);
+    if (s == QT_OK) s = collect_timing();
+    if (s == QT_OK) s = check_device_error();
+    return s;
+  }
+
+  // Shared default-choice prefix (QT_FLAG_SHARE_PREFIX).  Every trajectory
+  // of the run applies the same operators up to its first channel whose draw
+  // leaves the default operator (stage 1 fixes that point before any kernel
+  // runs), so the trajectories are taken in order of that point and one
+  // shared state advances along the default path: each trajectory copies the
+  // shared state at its divergence point and runs only its own suffix, and
+  // trajectories that never diverge are measured on the shared final state.
+  // The operations are those of the per-trajectory loop in the same order;
+  // only the boundaries of the fused pieces differ (the piece that straddles
+  // a divergence point is split, as at a flush point).
+  qt_status run_shared(float2* shared, float2* work, uint64_t* d_samples) {
+    const uint32_t T = R.T, nch = R.nch;
+    const uint32_t nops = static_cast<uint32_t>(c.ops.size());
+    std::vector<Stage1> plan(T);
+    std::vector<uint32_t> order(T);
+    for (uint32_t t = 0; t < T; ++t) {
+      stage1(t, plan[t]);
+      order[t] = t;
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [&](uint32_t a, uint32_t b) { return plan[a].diverge < plan[b].diverge; });
+    const std::vector<int> defaults = [&] {
+      std::vector<int> d(nch);
+      for (uint32_t ch = 0; ch < nch; ++ch) d[ch] = c.ops[c.channel_op[ch]].def;
+      return d;
+    }();
+    const std::vector<double> noscale(nch, 0.0);
+    const size_t sbytes = sizeof(float2) << R.n;
+    bool started = false;
+    uint32_t at = 0;                       // ops [0, at) applied to the shared state
+    for (uint32_t t : order) {
+      const Stage1& s1 = plan[t];
+      const uint32_t D = s1.diverge < nch ? c.channel_op[s1.diverge] : nops;
+      qt_status s = QT_OK;
+      if (!started) {
+        s = run_first_segment(shared, D, defaults, noscale);
+        started = true;
+      } else if (D > at) {
+        s = run_segment(shared, at, D, defaults, noscale);
+      }
+      if (s != QT_OK) return s;
+      at = std::max(at, D);
+      R.stats.prefix_ops += D;
+      float2* dst = R.p.keep_states ? R.states[t].as<float2>() : work;
+      if (s1.diverge == nch && !R.p.keep_states) {
+        s = finish_trajectory(t, shared, d_samples);   // the default path to the end
+        if (s != QT_OK) return s;
+        continue;
+      }
+      QT_CUDA(cudaMemcpyAsync(dst, shared, sbytes, cudaMemcpyDeviceToDevice, R.st), "cudaMemcpyAsync(prefix)");
+      R.stats.prefix_copies++;
+      if (s1.diverge < nch) {
+        s = run_from(t, dst, s1, D);
+        if (s != QT_OK) return s;
+      }
+      s = finish_trajectory(t, dst, d_samples);
+      if (s != QT_OK) return s;
     }
     return QT_OK;
   }
@@ -717,9 +817,14 @@ qt_status qt_run_trajectories(const qt_fused* f, const qt_run_params* p, qt_run*
     R->stats.h2d_bytes += sizeof(double) * 2 * c.n;
   }
   const size_t sbytes = sizeof(float2) << c.n;
-  DevBuf work, dsamp;
+  // shared default-choice prefix: delayed mode only (the conventional
+  // algorithm evaluates every channel, so no two trajectories share a prefix)
+  const bool share = (p->flags & QT_FLAG_SHARE_PREFIX) && p->mode == QT_DELAYED && p->num_traj > 1;
+  DevBuf work, dsamp, shared;
   if (!p->keep_states && !work.alloc(sbytes, R->st))
     return set_error(QT_ERR_OUT_OF_MEMORY, "qt_run_trajectories: state allocation (%zu bytes)", sbytes);
+  if (share && !shared.alloc(sbytes, R->st))
+    return set_error(QT_ERR_OUT_OF_MEMORY, "qt_run_trajectories: shared-prefix state allocation (%zu bytes)", sbytes);
   if (p->keep_states) {
     R->states.resize(R->T);
     for (uint32_t t = 0; t < R->T; ++t)
@@ -736,16 +841,17 @@ qt_status qt_run_trajectories(const qt_fused* f, const qt_run_params* p, qt_run*
   QT_CUDA(cudaEventCreate(&e1), "cudaEventCreate");
   struct EvGuard { cudaEvent_t a, b; ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); } } eg{e0, e1};
   QT_CUDA(cudaEventRecord(e0, R->st), "cudaEventRecord");
-  for (uint32_t t = 0; t < R->T; ++t) {
-    float2* psi = p->keep_states ? R->states[t].as<float2>() : work.as<float2>();
-    qt_status s = ctl.trajectory(t, psi);
+  if (share) {
+    qt_status s = ctl.run_shared(shared.as<float2>(), work.as<float2>(), dsamp.as<uint64_t>());
     if (s != QT_OK) return s;
-    s = ctl.measure(t, psi, dsamp.as<uint64_t>());
-    if (s != QT_OK) return s;
-    s = ctl.collect_timing();
-    if (s != QT_OK) return s;
-    s = ctl.check_device_error();
-    if (s != QT_OK) return s;
+  } else {
+    for (uint32_t t = 0; t < R->T; ++t) {
+      float2* psi = p->keep_states ? R->states[t].as<float2>() : work.as<float2>();
+      qt_status s = ctl.trajectory(t, psi);
+      if (s != QT_OK) return s;
+      s = ctl.finish_trajectory(t, psi, dsamp.as<uint64_t>());
+      if (s != QT_OK) return s;
+    }
   }
   QT_CUDA(cudaEventRecord(e1, R->st), "cudaEventRecord");
   if (nsamp) {

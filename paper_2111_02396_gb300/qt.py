@@ -28,6 +28,7 @@ QT_DELAYED, QT_EAGER = 0, 1
 QT_FP32, QT_TF32X3 = 0, 1
 QT_FLAG_TIME_KERNELS = 1
 QT_FLAG_MULTI_GATE = 2
+QT_FLAG_SHARE_PREFIX = 4
 
 
 class QtError(RuntimeError):
@@ -58,7 +59,8 @@ class qt_run_stats_t(C.Structure):
                 ("apply_bytes", C.c_uint64), ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64),
                 ("kernel_launches", C.c_uint64), ("fused_pieces", C.c_uint64),
                 ("passes_by_width", C.c_uint64 * 8), ("apply_ms_by_width", C.c_double * 8),
-                ("folded_pieces", C.c_uint64), ("fold_split", C.c_uint32), ("pad", C.c_uint32)]
+                ("folded_pieces", C.c_uint64), ("fold_split", C.c_uint32), ("pad", C.c_uint32),
+                ("prefix_copies", C.c_uint64), ("prefix_ops", C.c_uint64)]
 
 
 class qt_fused_info_t(C.Structure):
@@ -370,9 +372,11 @@ class Fused:
 class Run:
     def __init__(self, fused: Fused, num_traj, *, seed=0, first_traj=0, mode=QT_DELAYED,
                  precision=QT_FP32, samples_per_traj=0, z_masks=(), keep_states=False,
-                 time_kernels=False, grouping=False, readout_error=None, stream=None):
+                 time_kernels=False, grouping=False, share_prefix=False, readout_error=None, stream=None):
         """readout_error: None, or [n, 2] readout error probabilities per qubit,
-        (P(read 1 | 0), P(read 0 | 1)), applied to the samples (Sec. V.A)."""
+        (P(read 1 | 0), P(read 0 | 1)), applied to the samples (Sec. V.A).
+        share_prefix: trajectories share the state along the default-choice prefix
+        (QT_FLAG_SHARE_PREFIX, delayed mode)."""
         lib = load()
         self.fused = fused
         self.masks = np.ascontiguousarray(np.asarray(z_masks, dtype=np.uint64))
@@ -385,7 +389,8 @@ class Run:
         p.num_z_masks = len(self.masks)
         p.z_masks = self.masks.ctypes.data if len(self.masks) else None
         p.keep_states = 1 if keep_states else 0
-        p.flags = (QT_FLAG_TIME_KERNELS if time_kernels else 0) | (QT_FLAG_MULTI_GATE if grouping else 0)
+        p.flags = ((QT_FLAG_TIME_KERNELS if time_kernels else 0) | (QT_FLAG_MULTI_GATE if grouping else 0) |
+                   (QT_FLAG_SHARE_PREFIX if share_prefix else 0))
         p.stream = stream
         p.readout_error = self._ro.ctypes.data if self._ro is not None else None
         self.params = p

@@ -29,11 +29,12 @@ def qt():
 
 
 def compare_run(qt, orc, circ, T, *, k, mode, seed=0, S=0, masks=(), check_states=True,
-                precision=0, grouping=False):
+                precision=0, grouping=False, share_prefix=False):
     qc = qt.Circuit.from_synth(circ)
     f = qt.Fused(qc, k)
     run = qt.Run(f, T, seed=seed, mode=mode, samples_per_traj=S, z_masks=masks,
-                 keep_states=check_states, precision=precision, grouping=grouping)
+                 keep_states=check_states, precision=precision, grouping=grouping,
+                 share_prefix=share_prefix)
     kr, st = run.kraus_indices()
     omode = orc.DELAYED if mode == qt.QT_DELAYED else orc.EAGER
     ref = orc.run_trajectories(circ, T, mode=omode, seed=seed, keep_states=True)
@@ -201,6 +202,48 @@ def test_product_state_start_large_split(qt, orc, rows, cols):
     st = run.stats()
     assert st["folded_pieces"] > 0
     assert n - 20 <= st["fold_split"] <= 20
+
+
+@pytest.mark.parametrize("keep", [True, False])
+def test_shared_prefix_matches_oracle(qt, orc, keep):
+    """QT_FLAG_SHARE_PREFIX: trajectories copy one shared state at their first
+    non-default channel and run only their own suffix.  Branch records, states,
+    samples and expectations against the FP64 oracle: on a 20-qubit grid with
+    flushes (most trajectories diverge early), on a 15-qubit grid with weak
+    damping (most never diverge and are measured on the shared final state),
+    and on the 10-qubit chain workload."""
+    strong = qs.config1_circuit(rows=4, cols=5, depth=12, gamma=1e-2, lam=1e-2)
+    run, ref = compare_run(qt, orc, strong, 6, k=4, mode=qt.QT_DELAYED, seed=3, S=100,
+                           masks=[1, 0xfffff], check_states=keep, share_prefix=True)
+    st = run.stats()
+    assert st["flushes"] == int(np.sum(ref["stage"] == 2)) and st["flushes"] > 0
+    assert st["prefix_copies"] > 0
+    weak = qs.config1_circuit(rows=3, cols=5, depth=16)
+    run, ref = compare_run(qt, orc, weak, 12, k=4, mode=qt.QT_DELAYED, seed=1, S=100,
+                           masks=[1, 0x7fff], check_states=keep, share_prefix=True)
+    kr = run.kraus_indices()[0]
+    never = int(np.sum(np.all(ref["stage"] == 1, axis=1) & np.all(kr == 0, axis=1)))
+    assert never >= 3                              # measured on the shared final state
+    st = run.stats()
+    assert st["prefix_ops"] > 0
+    if not keep:
+        assert st["prefix_copies"] <= 12 - never
+    compare_run(qt, orc, qs.config0_circuit(), 64, k=2, mode=qt.QT_DELAYED, S=100,
+                masks=[1, 1023], check_states=keep, share_prefix=True)
+
+
+def test_shared_prefix_equals_per_trajectory_loop(qt):
+    """Sharing the prefix changes only where fused pieces are split: the same branch
+    records, states within one kernel call's rounding, and fewer fused passes."""
+    circ = qs.config1_circuit(rows=4, cols=5, depth=16, gamma=2e-3, lam=2e-3)
+    f = qt.Fused(qt.Circuit.from_synth(circ), 4)
+    a = qt.Run(f, 16, seed=9, keep_states=True, share_prefix=True)
+    b = qt.Run(f, 16, seed=9, keep_states=True)
+    np.testing.assert_array_equal(a.kraus_indices()[0], b.kraus_indices()[0])
+    np.testing.assert_array_equal(a.kraus_indices()[1], b.kraus_indices()[1])
+    for t in range(16):
+        assert rel_l2(a.state(t), b.state(t)) < 2e-6
+    assert a.stats()["fused_passes"] < b.stats()["fused_passes"]
 
 
 def test_mixture_only_circuit_never_flushes(qt, orc):
