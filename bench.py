@@ -427,23 +427,23 @@ def batched_form(steps=3, warmup=2, num=8192, plain_stride=32, uuid=None):
     stream = torch.cuda.Stream()
     sh = stream.cuda_stream
     t0 = time.perf_counter()
-    best_k, best_t, table = pkg.autotune_batch(qcs, sample=256, kmin=2, kmax=6, stream=sh)
+    tune, table = pkg.autotune_batch(qcs, sample=256, kmin=2, kmax=6, stream=sh)
     t_tune = time.perf_counter() - t0
     t0 = time.perf_counter()
-    fused = pkg.fuse_many(qcs, best_k)
+    fused = pkg.fuse_by_class(qcs, tune)
     t_fuse = time.perf_counter() - t0
     t0 = time.perf_counter()
     batch = pkg.Batch(fused)
     t_pack = time.perf_counter() - t0
+    launch = dict(use_graph=True, threads=tune["threads_shared"], threads_global=tune["threads_global"], stream=sh)
     for i in range(warmup):
-        batch.run(seed=0, first_traj=i * num, samples_per_traj=SAMPLES, use_graph=True, threads=best_t, stream=sh)
+        batch.run(seed=0, first_traj=i * num, samples_per_traj=SAMPLES, **launch)
     clk = ClockSampler(uuid)
     torch.cuda.synchronize()
     clk.start()
     ms = []
     for i in range(steps):
-        batch.run(seed=0, first_traj=(warmup + i) * num, samples_per_traj=SAMPLES, use_graph=True,
-                  threads=best_t, stream=sh)
+        batch.run(seed=0, first_traj=(warmup + i) * num, samples_per_traj=SAMPLES, **launch)
         ms.append(batch.stats()["device_ms"])
     clocks = clk.stop()
     batched = num / (statistics.median(ms) / 1e3)
@@ -484,7 +484,7 @@ def batched_form(steps=3, warmup=2, num=8192, plain_stride=32, uuid=None):
     return {
         "workload": BATCH_WORKLOAD, "trajectories_per_run": num, "runs": steps, "warmup_runs": warmup,
         "traj_per_s": batched, "ms_per_run": statistics.median(ms),
-        "fuse_k": best_k, "threads_per_cta": best_t, "cuda_graph": True,
+        "autotuned": tune, "cuda_graph": True,
         "plain_loop": {"traj_per_s": plain,
                        "sample": f"every {plain_stride}th circuit ({len(idx)} trajectories), qt_run_trajectories "
                                  f"one trajectory at a time on the same GPU, scaled by {plain_stride}"},
@@ -496,7 +496,7 @@ def batched_form(steps=3, warmup=2, num=8192, plain_stride=32, uuid=None):
                                         "<= 2^14 amplitudes live in shared memory, so this is not an HBM figure"},
         "l2_err_max": max(errs) if errs else None,
         "l2_err_sample": f"{len(errs)} trajectories (2 of each n in 8, 10, .., 18) against the FP64 oracle",
-        "autotune": {f"k{k}_t{t}": v for (k, t), v in table.items()},
+        "autotune_ms": {f"{c}_k{k}_t{t}": v for (c, k, t), v in table.items()},
         "cpu_baseline": {"value": len(sample_o) / t_orc, "unit": UNIT, "cores": len(os.sched_getaffinity(0)),
                          "kind": "oracle",
                          "sample": f"every {stride_o}th circuit ({len(sample_o)} trajectories with {SAMPLES} "

@@ -301,8 +301,11 @@ typedef struct {
   uint32_t samples_per_traj;   /* bitstrings per final state */
   uint32_t keep_states;        /* 1: keep final states for qt_batch_state */
   uint32_t use_graph;          /* replay the launch sequence as a CUDA graph (needs a stream) */
-  uint32_t threads;            /* CTA size: 128, 256 or 512 (0 = 512) */
+  uint32_t threads;            /* CTA size of trajectories whose states fit in shared memory
+                                  (n <= 14): 128, 256 or 512 (0 = 512) */
   void* stream;                /* cudaStream_t */
+  uint32_t threads_global;     /* CTA size of trajectories whose states live in global memory
+                                  (n > 14): 128, 256 or 512 (0 = threads) */
 } qt_batch_params;
 
 /* Run one trajectory of every circuit of the batch (Alg. 2, the same draws
@@ -323,13 +326,23 @@ typedef struct {
 } qt_batch_stats_t;
 qt_status qt_batch_stats(const qt_batch* b, qt_batch_stats_t* out);
 void qt_batch_destroy(qt_batch* b);
-/* Autotuner of the batched form: on a spread sample of `sample` circuits
- * (0 = 256) it fuses at every width kmin..kmax (<= 6), times the batched
- * kernel (warm-up + 2 timed runs) at 128, 256 and 512 threads per CTA, and
- * returns the fastest width and CTA size.  table (optional) receives the
- * mean ms per run, [(k - kmin) * 3 + {128, 256, 512}]. */
+/* Autotuner of the batched form.  The batched kernel runs two classes of
+ * trajectories: states of <= 2^14 amplitudes held in a CTA's shared memory,
+ * and larger states streamed from a per-CTA slot of global memory.  Their
+ * costs differ (the first is bound by latency and arithmetic, the second by
+ * memory traffic), so each class is tuned on its own spread sample of at
+ * most `sample` circuits (0 = 256): every fusion width kmin..kmax (<= 6) at
+ * 128, 256 and 512 threads per CTA (warm-up + 2 timed runs).  best receives
+ * the fastest width and CTA size of each class (a class absent from the
+ * batch keeps kmin and 512); table (optional, 2 * (kmax - kmin + 1) * 3
+ * doubles) the mean ms per run, [(class * (kmax - kmin + 1) + k - kmin) * 3
+ * + {128, 256, 512}], class 0 = shared memory, 1 = global memory. */
+typedef struct {
+  uint32_t k_shared, threads_shared;   /* n <= 14 */
+  uint32_t k_global, threads_global;   /* n > 14 */
+} qt_batch_tuning;
 qt_status qt_batch_autotune(uint32_t num, const qt_circuit* const* circuits, uint32_t sample, uint32_t kmin,
-                            uint32_t kmax, void* stream, uint32_t* best_k, uint32_t* best_threads, double* table);
+                            uint32_t kmax, void* stream, qt_batch_tuning* best, double* table);
 
 /* ---------------------------------------------------------------------- */
 /* Serving form: a request loop with continuous batching                  */

@@ -14,5 +14,5 @@ from .qt import (  # noqa: F401
     QT_DELAYED, QT_EAGER, QT_FP32, QT_TF32X3,
     qt_state_apply, qt_state_reduced_density, qt_state_sample, qt_state_expect_z, qt_state_cdf,
     kernel_arch,
-    Batch, fuse_many, autotune_batch, Server,
+    Batch, fuse_many, fuse_by_class, autotune_batch, Server,
 )

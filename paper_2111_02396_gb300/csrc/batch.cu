@@ -192,22 +192,171 @@ __device__ __noinline__ void cta_apply_wide(float2* psi, int n, const int* order
   }
 }
 
+__device__ __forceinline__ uint32_t insert_zeros32(uint32_t x, int w, const int* sorted) {
+  for (int b = 0; b < w; ++b) {
+    const int s = sorted[b];
+    x = ((x >> s) << (s + 1)) | (x & ((1u << s) - 1u));
+  }
+  return x;
+}
+
+// psi <- A psi for a state in global memory (n <= 20, so 32-bit indices):
+// each thread gathers NL = 16 amplitudes (B = 16 / 2^W sets, 64 KB per SM of
+// 512 threads) before any arithmetic, so that enough loads are in flight
+// to cover DRAM latency; each matrix entry is one broadcast 128-bit shared load,
+// (a.x, a.x, a.y, a.y), reused by the thread's B sets; a complex
+// multiply-add is two packed FP32x2 FMAs into P = sum a.x (v.x, v.y) and
+// Q = sum a.y (v.x, v.y), and the output is (P.x - Q.y, P.y + Q.x).
+template <int W>
+__device__ __noinline__ void cta_apply_glob(float2* __restrict__ psi, int n, const int* order,
+                                            const float4* __restrict__ A4) {
+  constexpr int D = 1 << W;
+  constexpr int NL = 16;
+  constexpr int B = NL / D;
+  int sorted[W];
+  uint32_t off[D];
+#pragma unroll
+  for (int b = 0; b < W; ++b) sorted[b] = order[b];
+#pragma unroll
+  for (int i = 1; i < W; ++i)
+#pragma unroll
+    for (int j = i; j > 0; --j)
+      if (sorted[j - 1] > sorted[j]) { const int t = sorted[j]; sorted[j] = sorted[j - 1]; sorted[j - 1] = t; }
+#pragma unroll
+  for (int m = 0; m < D; ++m) {
+    uint32_t o = 0;
+#pragma unroll
+    for (int b = 0; b < W; ++b)
+      if ((m >> b) & 1) o |= 1u << order[b];
+    off[m] = o;
+  }
+  const uint32_t sets = 1u << (n - W);
+  const uint32_t stride = blockDim.x;
+  for (uint32_t s0 = threadIdx.x; s0 < sets; s0 += B * stride) {
+    uint32_t base[B];
+    float2 v[B][D];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const uint32_t sb = s0 + b * stride;
+      base[b] = insert_zeros32(sb < sets ? sb : s0, W, sorted);
+#pragma unroll
+      for (int m = 0; m < D; ++m) v[b][m] = psi[base[b] | off[m]];
+    }
+    // rows one at a time: unrolling them lets the compiler hoist every
+    // matrix load of the pass into registers, which spills
+#pragma unroll 1
+    for (int j = 0; j < D; ++j) {
+      float2 P[B], Q[B];
+#pragma unroll
+      for (int b = 0; b < B; ++b) { P[b] = make_float2(0.f, 0.f); Q[b] = make_float2(0.f, 0.f); }
+#pragma unroll
+      for (int m = 0; m < D; ++m) {
+        const float4 a = A4[j * D + m];
+        const float2 ax = make_float2(a.x, a.y), ay = make_float2(a.z, a.w);
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+          P[b] = __ffma2_rn(ax, v[b][m], P[b]);
+          Q[b] = __ffma2_rn(ay, v[b][m], Q[b]);
+        }
+      }
+#pragma unroll
+      for (int b = 0; b < B; ++b)
+        if (s0 + b * stride < sets) psi[base[b] | off[j]] = make_float2(P[b].x - Q[b].y, P[b].y + Q[b].x);
+    }
+  }
+}
+
+// Aglob: the matrix in global memory (scaled by `scale` while staged), or
+// smat itself when the matrix was composed in shared memory (scale unused).
+template <bool GLOBAL>
 __device__ void cta_apply(float2* psi, int n, int w, const int* order, const float2* Aglob, float scale,
                           float2* smat) {
   const int D = 1 << w;
+  const bool staged = Aglob == smat;
   __syncthreads();                     // previous users of smat / psi are done
-  for (int i = threadIdx.x; i < D * D; i += blockDim.x) {
-    const float2 a = Aglob[i];
-    smat[i] = make_float2(a.x * scale, a.y * scale);
+  if (GLOBAL && w <= 4) {
+    float4* A4 = reinterpret_cast<float4*>(smat + (1u << (2 * kMaxW)));
+    for (int i = threadIdx.x; i < D * D; i += blockDim.x) {
+      const float2 a = Aglob[i];
+      const float x = staged ? a.x : a.x * scale, y = staged ? a.y : a.y * scale;
+      A4[i] = make_float4(x, x, y, y);
+    }
+    __syncthreads();
+    switch (w) {
+      case 1: cta_apply_glob<1>(psi, n, order, A4); break;
+      case 2: cta_apply_glob<2>(psi, n, order, A4); break;
+      case 3: cta_apply_glob<3>(psi, n, order, A4); break;
+      default: cta_apply_glob<4>(psi, n, order, A4); break;
+    }
+    return;
   }
-  __syncthreads();
-  switch (w) {
-    case 1: n > kSmemNMax ? cta_apply_w<1, true>(psi, n, order, smat) : cta_apply_w<1, false>(psi, n, order, smat); break;
-    case 2: n > kSmemNMax ? cta_apply_w<2, true>(psi, n, order, smat) : cta_apply_w<2, false>(psi, n, order, smat); break;
-    case 3: n > kSmemNMax ? cta_apply_w<3, true>(psi, n, order, smat) : cta_apply_w<3, false>(psi, n, order, smat); break;
-    case 4: n > kSmemNMax ? cta_apply_w<4, true>(psi, n, order, smat) : cta_apply_w<4, false>(psi, n, order, smat); break;
-    case 5: cta_apply_wide<5>(psi, n, order, smat); break;
-    default: cta_apply_wide<6>(psi, n, order, smat); break;
+  if (!staged) {
+    for (int i = threadIdx.x; i < D * D; i += blockDim.x) {
+      const float2 a = Aglob[i];
+      smat[i] = make_float2(a.x * scale, a.y * scale);
+    }
+    __syncthreads();
+  }
+  if (!GLOBAL) {
+    switch (w) {
+      case 1: cta_apply_w<1, false>(psi, n, order, smat); return;
+      case 2: cta_apply_w<2, false>(psi, n, order, smat); return;
+      case 3: cta_apply_w<3, false>(psi, n, order, smat); return;
+      case 4: cta_apply_w<4, false>(psi, n, order, smat); return;
+      default: break;
+    }
+  }
+  if (w == 5) cta_apply_wide<5>(psi, n, order, smat);
+  else cta_apply_wide<6>(psi, n, order, smat);
+}
+
+__device__ __forceinline__ float2 cmul_add(float2 a, float2 x, float2 acc) {
+  acc.x = fmaf(a.x, x.x, fmaf(-a.y, x.y, acc.x));
+  acc.y = fmaf(a.x, x.y, fmaf(a.y, x.x, acc.y));
+  return acc;
+}
+
+// M <- A M for the 2^q x 2^q operator A (q = 1, 2; index bit b <-> pos[b]
+// among the w basis bits of M), scaled by sc: every column of M is a vector
+// that A acts on, as in Alg. 1.  M is D x D row-major in shared memory.
+__device__ void cta_left_apply(float2* M, int w, int q, const int* pos, const float2* A, float sc) {
+  const int D = 1 << w;
+  if (q == 1) {
+    const float2 a00 = make_float2(A[0].x * sc, A[0].y * sc), a01 = make_float2(A[1].x * sc, A[1].y * sc);
+    const float2 a10 = make_float2(A[2].x * sc, A[2].y * sc), a11 = make_float2(A[3].x * sc, A[3].y * sc);
+    const int p = pos[0];
+    for (int u = threadIdx.x; u < (D >> 1) * D; u += blockDim.x) {
+      const int c = u & (D - 1), rr = u >> w;
+      const int r0 = ((rr >> p) << (p + 1)) | (rr & ((1 << p) - 1)), r1 = r0 | (1 << p);
+      const float2 x0 = M[r0 * D + c], x1 = M[r1 * D + c];
+      M[r0 * D + c] = cmul_add(a01, x1, cmul_add(a00, x0, make_float2(0.f, 0.f)));
+      M[r1 * D + c] = cmul_add(a11, x1, cmul_add(a10, x0, make_float2(0.f, 0.f)));
+    }
+    return;
+  }
+  const int lo = pos[0] < pos[1] ? pos[0] : pos[1], hi = pos[0] < pos[1] ? pos[1] : pos[0];
+  for (int u = threadIdx.x; u < (D >> 2) * D; u += blockDim.x) {
+    const int c = u & (D - 1);
+    int r = u >> w;
+    r = ((r >> lo) << (lo + 1)) | (r & ((1 << lo) - 1));
+    r = ((r >> hi) << (hi + 1)) | (r & ((1 << hi) - 1));
+    int rows[4];
+    float2 x[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      rows[m] = r | ((m & 1) << pos[0]) | (((m >> 1) & 1) << pos[1]);
+      x[m] = M[rows[m] * D + c];
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const float2 a = A[j * 4 + m];
+        acc = cmul_add(make_float2(a.x * sc, a.y * sc), x[m], acc);
+      }
+      M[rows[j] * D + c] = acc;
+    }
   }
 }
 
@@ -336,9 +485,14 @@ __device__ __forceinline__ int decide_stage1(const Set& st, const double* pbar, 
 // ---------------------------------------------------------------------------
 // the persistent kernel
 // ---------------------------------------------------------------------------
+// GLOBAL = false: the launch's trajectories have states of <= 2^14 amplitudes,
+// held in the CTA's shared memory; GLOBAL = true: larger states, held in a
+// per-CTA slot of global memory (shared memory then holds only the matrix)
+template <bool GLOBAL>
 __global__ void __launch_bounds__(512) k_batch(const __grid_constant__ Dev d) {
-  extern __shared__ __align__(16) float2 s_state[];
-  float2* s_mat = s_state + (1u << kSmemNMax);   // the pass's matrix, up to 64 x 64
+  extern __shared__ __align__(16) float2 s_dyn[];
+  float2* s_state = s_dyn;
+  float2* s_mat = GLOBAL ? s_dyn : s_dyn + (1u << kSmemNMax);   // the pass's matrix, up to 64 x 64
   __shared__ double s_red[32][17];
   __shared__ double s_rho[16];
   __shared__ double s_wcum[32];
@@ -361,7 +515,7 @@ __global__ void __launch_bounds__(512) k_batch(const __grid_constant__ Dev d) {
     const uint64_t seed = d.run[0];
     const uint64_t traj_id = d.run[1] + ti;
     float2* psi;
-    if (n <= kSmemNMax) psi = s_state;
+    if (!GLOBAL) psi = s_state;
     else psi = d.keep ? d.arena + T.arena_off : d.arena + static_cast<uint64_t>(blockIdx.x) * d.slot_amps;
     for (uint64_t x = tid; x < amps; x += blockDim.x) psi[x] = make_float2(x == 0 ? 1.f : 0.f, 0.f);
     // stage 1 of every channel from its draw and the lower bounds
@@ -417,25 +571,44 @@ __global__ void __launch_bounds__(512) k_batch(const __grid_constant__ Dev d) {
         if (dflt) {
           int order[kMaxW];
           for (int b = 0; b < G.w; ++b) order[b] = G.t[b];
-          cta_apply(psi, n, G.w, order, d.fmat + G.mat, 1.f, s_mat);
+          cta_apply<GLOBAL>(psi, n, G.w, order, d.fmat + G.mat, 1.f, s_mat);
           continue;
         }
+        // a piece that is cut by the segment or holds a non-default operator:
+        // its members in [lo, hi) are composed in FP32 in shared memory into
+        // one matrix over the gate's qubits (identity on qubits none of them
+        // touches), then applied in one pass
+        const int D = 1 << G.w;
+        __syncthreads();                 // previous users of s_mat are done
+        for (int i = tid; i < D * D; i += blockDim.x)
+          s_mat[i] = make_float2((i >> G.w) == (i & (D - 1)) ? 1.f : 0.f, 0.f);
         for (uint32_t mi = 0; mi < G.nmem; ++mi) {
           const uint32_t pos = d.members[G.mem0 + mi];
           if (pos < lo || pos >= hi) continue;
           const Op op = d.ops[T.op0 + pos];
           const Set st = d.sets[op.set];
-          int order[2] = {op.q0, op.q1};
           const uint32_t dd = 1u << (2 * op.q);
+          const float2* A;
+          float sc = 1.f;
           if (op.channel < 0) {
-            cta_apply(psi, n, op.q, order, d.fmat + st.mat, 1.f, s_mat);
+            A = d.fmat + st.mat;
           } else if (static_cast<int>(pos) == pend_pos) {
-            cta_apply(psi, n, op.q, order, d.fmat + st.kraus + pend_choice * dd, pend_scale, s_mat);
+            A = d.fmat + st.kraus + pend_choice * dd;
+            sc = pend_scale;
           } else {
-            const int ci = d.kraus[T.ch0 + op.channel];
-            cta_apply(psi, n, op.q, order, d.fmat + st.mat + ci * dd, 1.f, s_mat);
+            A = d.fmat + st.mat + d.kraus[T.ch0 + op.channel] * dd;
           }
+          int p[2] = {0, 0};
+          for (int b = 0; b < G.w; ++b) {
+            if (G.t[b] == op.q0) p[0] = b;
+            if (op.q > 1 && G.t[b] == op.q1) p[1] = b;
+          }
+          __syncthreads();               // the previous member's update is complete
+          cta_left_apply(s_mat, G.w, op.q, p, A, sc);
         }
+        int order[kMaxW];
+        for (int b = 0; b < G.w; ++b) order[b] = G.t[b];
+        cta_apply<GLOBAL>(psi, n, G.w, order, s_mat, 1.f, s_mat);
       }
       if (fch < 0) break;
       // stage 2 at the flush point (Alg. 2 steps 12-20)
@@ -501,7 +674,7 @@ __global__ void __launch_bounds__(512) k_batch(const __grid_constant__ Dev d) {
     }
     __syncthreads();
     if (d.S) cta_sample(psi, n, seed, traj_id, d.S, d.samples + static_cast<uint64_t>(ti) * d.S, s_wcum);
-    if (d.keep && n <= kSmemNMax) {
+    if (d.keep && !GLOBAL) {
       __syncthreads();
       for (uint64_t x = tid; x < amps; x += blockDim.x) d.arena[T.arena_off + x] = psi[x];
     }
@@ -584,14 +757,23 @@ struct qt_batch {
   std::vector<uint32_t> flushes;
   double device_ms = 0.0;
   uint64_t gate_ops = 0, fused_gates = 0;
+  // trajectories with states in global memory (n > 14) come first in `order`;
+  // the two classes run as two persistent launches, the second on a side
+  // stream so that its CTAs take SMs as the first launch's CTAs retire
+  uint32_t nglob = 0;
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // CUDA graph of the launch sequence
   cudaGraphExec_t gexec = nullptr;
   cudaGraph_t graph = nullptr;
-  uint32_t g_threads = 0, g_S = 0, g_keep = 0;
+  uint32_t g_threads = 0, g_threads_glob = 0, g_S = 0, g_keep = 0;
   ~qt_batch() {
     if (gexec) cudaGraphExecDestroy(gexec);
     if (graph) cudaGraphDestroy(graph);
     if (hrun) cudaFreeHost(hrun);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (side) cudaStreamDestroy(side);
   }
 };
 
@@ -774,6 +956,7 @@ qt_status qt_batch_create(uint32_t num, const qt_fused* const* fused, qt_batch**
   for (uint32_t i = 0; i < num; ++i) {
     B->traj[i].arena_off = B->total_amps;
     B->total_amps += 1ull << B->traj[i].n;
+    if (B->traj[i].n > static_cast<uint32_t>(bt::kSmemNMax)) B->nglob++;
   }
   // ---- one device buffer for all tables ----
   auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
@@ -813,13 +996,17 @@ qt_status qt_batch_create(uint32_t num, const qt_fused* const* fused, qt_batch**
   d.dmat = reinterpret_cast<const double*>(base + o_dmat);
   d.order = reinterpret_cast<const uint32_t*>(base + o_order);
   d.num = num;
-  // counter (4 B), error flag (4 B), run parameters at +16 (2 x 8 B)
+  // work counters of the two launches (2 x 4 B), error flag (4 B), run parameters at +16 (2 x 8 B)
   if (!B->counter.alloc(32)) return set_error(QT_ERR_OUT_OF_MEMORY, "qt_batch_create: counter");
   d.counter = static_cast<unsigned int*>(B->counter.p);
-  d.err = reinterpret_cast<int*>(static_cast<unsigned int*>(B->counter.p) + 1);
+  d.err = reinterpret_cast<int*>(static_cast<unsigned int*>(B->counter.p) + 2);
   d.run = reinterpret_cast<const uint64_t*>(static_cast<uint8_t*>(B->counter.p) + 16);
   if (cudaMallocHost(&B->hrun, 2 * sizeof(uint64_t)) != cudaSuccess)
     return set_error(QT_ERR_OUT_OF_MEMORY, "qt_batch_create: pinned parameters");
+  if (cudaStreamCreateWithFlags(&B->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&B->ev_join, cudaEventDisableTiming) != cudaSuccess)
+    return set_error(QT_ERR_CUDA, "qt_batch_create: side stream");
   *out = B.release();
   return QT_OK;
 }
@@ -829,8 +1016,10 @@ qt_status qt_batch_run(qt_batch* b, const qt_batch_params* p) {
   if (!b || !p) return set_error(QT_ERR_INVALID_ARG, "qt_batch_run: NULL argument");
   if (p->samples_per_traj > 1u << 20) return set_error(QT_ERR_INVALID_ARG, "qt_batch_run: samples_per_traj too large");
   const uint32_t threads = p->threads ? p->threads : 512;
-  if (threads != 128 && threads != 256 && threads != 512)
-    return set_error(QT_ERR_INVALID_ARG, "qt_batch_run: threads %u (128, 256 or 512)", threads);
+  const uint32_t threads_glob = p->threads_global ? p->threads_global : threads;
+  for (uint32_t t : {threads, threads_glob})
+    if (t != 128 && t != 256 && t != 512)
+      return set_error(QT_ERR_INVALID_ARG, "qt_batch_run: threads %u (128, 256 or 512)", t);
   cudaStream_t st = static_cast<cudaStream_t>(p->stream);
   bt::Dev& d = b->dev;
   const bool relayout = !b->outs.p || p->samples_per_traj != b->S || (p->keep_states != 0) != (b->keep != 0);
@@ -870,14 +1059,28 @@ qt_status qt_batch_run(qt_batch* b, const qt_batch_params* p) {
   }
   b->hrun[0] = p->seed;
   b->hrun[1] = p->first_traj;
-  const size_t smem = (sizeof(float2) << bt::kSmemNMax) + sizeof(float2) * (1u << (2 * bt::kMaxW));
+  // the matrix area (64 x 64 complex64) and, for global states, its 16 x 16
+  // (x, x, y, y) expansion behind it
+  const size_t smem_mat = sizeof(float2) * (1u << (2 * bt::kMaxW)) + sizeof(float4) * 256;
+  const size_t smem = (sizeof(float2) << bt::kSmemNMax) + smem_mat;
   static PerDevice attr_set;
   const cudaError_t attr = static_cast<cudaError_t>(attr_set.get([&] {
-    return static_cast<int>(
-        cudaFuncSetAttribute(bt::k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    cudaError_t e1 = cudaFuncSetAttribute(bt::k_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          static_cast<int>(smem));
+    if (e1 == cudaSuccess)
+      e1 = cudaFuncSetAttribute(bt::k_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(smem_mat));
+    return static_cast<int>(e1);
   }));
   if (attr != cudaSuccess) return set_error(QT_ERR_CUDA, "qt_batch_run: smem attribute: %s", cudaGetErrorString(attr));
-  const unsigned grid = static_cast<unsigned>(std::min<uint64_t>(sm_count(), b->num));
+  const uint32_t nglob = b->nglob, nsh = b->num - b->nglob;
+  const unsigned grid_g = static_cast<unsigned>(std::min<uint64_t>(sm_count(), nglob));
+  const unsigned grid_s = static_cast<unsigned>(std::min<uint64_t>(sm_count(), nsh));
+  bt::Dev dg = d, ds = d;
+  dg.num = nglob;
+  ds.order = d.order + nglob;
+  ds.num = nsh;
+  ds.counter = d.counter + 1;
   struct Events {                   // the run's timing events, destroyed on every return
     cudaEvent_t a = nullptr, b = nullptr;
     ~Events() {
@@ -893,16 +1096,28 @@ qt_status qt_batch_run(qt_batch* b, const qt_batch_params* p) {
     cudaError_t r = cudaMemcpyAsync(static_cast<uint8_t*>(b->counter.p) + 16, b->hrun, 2 * sizeof(uint64_t),
                                     cudaMemcpyHostToDevice, s);
     if (r != cudaSuccess) return r;
-    r = cudaMemsetAsync(b->counter.p, 0, sizeof(unsigned int) + sizeof(int), s);
+    r = cudaMemsetAsync(b->counter.p, 0, 2 * sizeof(unsigned int) + sizeof(int), s);
     if (r != cudaSuccess) return r;
-    bt::k_batch<<<grid, threads, smem, s>>>(d);
-    return cudaGetLastError();
+    const bool both = nglob && nsh;
+    if (both) {
+      r = cudaEventRecord(b->ev_fork, s);
+      if (r == cudaSuccess) r = cudaStreamWaitEvent(b->side, b->ev_fork, 0);
+      if (r != cudaSuccess) return r;
+    }
+    if (nglob) bt::k_batch<true><<<grid_g, threads_glob, smem_mat, s>>>(dg);
+    if (nsh) bt::k_batch<false><<<grid_s, threads, smem, both ? b->side : s>>>(ds);
+    r = cudaGetLastError();
+    if (r == cudaSuccess && both) {
+      r = cudaEventRecord(b->ev_join, b->side);
+      if (r == cudaSuccess) r = cudaStreamWaitEvent(s, b->ev_join, 0);
+    }
+    return r;
   };
   e = cudaEventRecord(e0, st);
   if (e == cudaSuccess && p->use_graph && st) {
     // the graph copies the run parameters from pinned memory when it runs, so
     // it is rebuilt only when the launch shape changes
-    if (b->gexec && b->g_threads != threads) {
+    if (b->gexec && (b->g_threads != threads || b->g_threads_glob != threads_glob)) {
       cudaGraphExecDestroy(b->gexec); b->gexec = nullptr;
       cudaGraphDestroy(b->graph); b->graph = nullptr;
     }
@@ -915,6 +1130,7 @@ qt_status qt_batch_run(qt_batch* b, const qt_batch_params* p) {
       }
       if (e == cudaSuccess) e = cudaGraphInstantiate(&b->gexec, b->graph, 0);
       b->g_threads = threads;
+      b->g_threads_glob = threads_glob;
     }
     if (e == cudaSuccess) e = cudaGraphLaunch(b->gexec, st);
   } else if (e == cudaSuccess) {
@@ -1000,46 +1216,64 @@ qt_status qt_batch_stats(const qt_batch* b, qt_batch_stats_t* out) {
 void qt_batch_destroy(qt_batch* b) { delete b; }
 
 qt_status qt_batch_autotune(uint32_t num, const qt_circuit* const* circuits, uint32_t sample, uint32_t kmin,
-                            uint32_t kmax, void* stream, uint32_t* best_k, uint32_t* best_threads, double* table) {
+                            uint32_t kmax, void* stream, qt_batch_tuning* best, double* table) {
   clear_error();
-  if (!circuits || !best_k || !best_threads || num == 0)
+  if (!circuits || !best || num == 0)
     return set_error(QT_ERR_INVALID_ARG, "qt_batch_autotune: NULL argument or empty batch");
   kmin = std::max<uint32_t>(kmin, 1);
   kmax = std::min<uint32_t>(kmax, bt::kMaxW);
   if (kmin > kmax) return set_error(QT_ERR_INVALID_ARG, "qt_batch_autotune: empty k range");
-  // a spread sample of the batch (every stride-th circuit)
-  const uint32_t ns = std::max<uint32_t>(1, std::min(sample ? sample : 256u, num));
-  std::vector<const qt_circuit*> sub(ns);
-  for (uint32_t i = 0; i < ns; ++i) sub[i] = circuits[static_cast<uint64_t>(i) * num / ns];
   static const uint32_t kThreadOpts[3] = {128, 256, 512};
-  double best = 1e300;
-  *best_k = kmin;
-  *best_threads = 512;
-  for (uint32_t k = kmin; k <= kmax; ++k) {
-    std::vector<qt_fused*> f(ns, nullptr);
-    qt_status s = qt_fuse_many(ns, sub.data(), k, 0, f.data());
-    if (s != QT_OK) return s;
-    qt_batch* b = nullptr;
-    s = qt_batch_create(ns, const_cast<const qt_fused* const*>(f.data()), &b);
-    for (auto* x : f) qt_fused_destroy(x);
-    if (s != QT_OK) return s;
-    for (int ti = 0; ti < 3; ++ti) {
-      qt_batch_params p{};
-      p.seed = 0x5eed;
-      p.samples_per_traj = 16;
-      p.threads = kThreadOpts[ti];
-      p.stream = stream;
-      double ms = 0.0;
-      for (int rep = 0; rep < 3 && s == QT_OK; ++rep) {
-        p.first_traj = rep;
-        s = qt_batch_run(b, &p);
-        if (rep > 0) ms += b->device_ms;     // the first run is warm-up
-      }
-      if (s != QT_OK) { qt_batch_destroy(b); return s; }
-      if (table) table[(k - kmin) * 3 + ti] = ms / 2.0;
-      if (ms < best) { best = ms; *best_k = k; *best_threads = kThreadOpts[ti]; }
+  const uint32_t nk = kmax - kmin + 1;
+  best->k_shared = best->k_global = kmin;
+  best->threads_shared = best->threads_global = 512;
+  if (table)
+    for (uint32_t i = 0; i < 2 * nk * 3; ++i) table[i] = 0.0;
+  // the two classes of the batched kernel: states in shared memory (n <= 14)
+  // and states in global memory, each tuned on a spread sample of its own
+  for (int cls = 0; cls < 2; ++cls) {
+    std::vector<const qt_circuit*> members;
+    for (uint32_t i = 0; i < num; ++i) {
+      if (!circuits[i]) return set_error(QT_ERR_INVALID_ARG, "qt_batch_autotune: circuit %u is NULL", i);
+      if ((circuits[i]->n > static_cast<uint32_t>(bt::kSmemNMax)) == (cls == 1)) members.push_back(circuits[i]);
     }
-    qt_batch_destroy(b);
+    if (members.empty()) continue;
+    const uint32_t nm = static_cast<uint32_t>(members.size());
+    const uint32_t ns = std::max<uint32_t>(1, std::min(sample ? sample : 256u, nm));
+    std::vector<const qt_circuit*> sub(ns);
+    for (uint32_t i = 0; i < ns; ++i) sub[i] = members[static_cast<uint64_t>(i) * nm / ns];
+    double best_ms = 1e300;
+    for (uint32_t k = kmin; k <= kmax; ++k) {
+      std::vector<qt_fused*> f(ns, nullptr);
+      qt_status s = qt_fuse_many(ns, sub.data(), k, 0, f.data());
+      if (s != QT_OK) return s;
+      qt_batch* b = nullptr;
+      s = qt_batch_create(ns, const_cast<const qt_fused* const*>(f.data()), &b);
+      for (auto* x : f) qt_fused_destroy(x);
+      if (s != QT_OK) return s;
+      for (int ti = 0; ti < 3; ++ti) {
+        qt_batch_params p{};
+        p.seed = 0x5eed;
+        p.samples_per_traj = 16;
+        p.threads = kThreadOpts[ti];
+        p.threads_global = kThreadOpts[ti];
+        p.stream = stream;
+        double ms = 0.0;
+        for (int rep = 0; rep < 3 && s == QT_OK; ++rep) {
+          p.first_traj = rep;
+          s = qt_batch_run(b, &p);
+          if (rep > 0) ms += b->device_ms;     // the first run is warm-up
+        }
+        if (s != QT_OK) { qt_batch_destroy(b); return s; }
+        if (table) table[(cls * nk + (k - kmin)) * 3 + ti] = ms / 2.0;
+        if (ms < best_ms) {
+          best_ms = ms;
+          if (cls == 0) { best->k_shared = k; best->threads_shared = kThreadOpts[ti]; }
+          else { best->k_global = k; best->threads_global = kThreadOpts[ti]; }
+        }
+      }
+      qt_batch_destroy(b);
+    }
   }
   return QT_OK;
 }

@@ -71,7 +71,7 @@ class qt_fused_info_t(C.Structure):
 class qt_batch_params(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("first_traj", C.c_uint64), ("samples_per_traj", C.c_uint32),
                 ("keep_states", C.c_uint32), ("use_graph", C.c_uint32), ("threads", C.c_uint32),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("threads_global", C.c_uint32)]
 
 
 class qt_batch_stats_t(C.Structure):
@@ -180,7 +180,7 @@ def load(build_if_missing: bool = True):
             "qt_batch_kraus_indices": [P, u32, P, P, C.c_size_t, P],
             "qt_batch_state": [P, u32, P, C.c_size_t],
             "qt_batch_stats": [P, P],
-            "qt_batch_autotune": [u32, P, u32, u32, u32, P, P, P, P],
+            "qt_batch_autotune": [u32, P, u32, u32, u32, P, P, P],
             "qt_server_create": [P, P],
             "qt_server_submit": [P, P, P, P],
             "qt_server_poll": [P, u64, P],
@@ -525,12 +525,15 @@ class Batch:
         self.S = 0
 
     def run(self, seed=0, first_traj=0, samples_per_traj=0, keep_states=False, use_graph=False,
-            threads=0, stream=None):
+            threads=0, threads_global=0, stream=None):
+        """threads: CTA size for states in shared memory (n <= 14); threads_global:
+        for larger states (0 = threads)."""
         p = qt_batch_params()
         p.seed, p.first_traj, p.samples_per_traj = seed, first_traj, samples_per_traj
         p.keep_states = 1 if keep_states else 0
         p.use_graph = 1 if use_graph else 0
         p.threads = threads
+        p.threads_global = threads_global
         p.stream = stream
         _check(load().qt_batch_run(self.h, C.byref(p)))
         self.S = samples_per_traj
@@ -567,20 +570,44 @@ class Batch:
             self.h = None
 
 
+class qt_batch_tuning(C.Structure):
+    _fields_ = [("k_shared", C.c_uint32), ("threads_shared", C.c_uint32),
+                ("k_global", C.c_uint32), ("threads_global", C.c_uint32)]
+
+
+SMEM_N_MAX = 14   # largest state (qubits) the batched kernel holds in shared memory
+
+
 def autotune_batch(circuits, sample=256, kmin=2, kmax=4, stream=None):
-    """qt_batch_autotune: returns (best_k, best_threads, {(k, threads): ms})."""
+    """qt_batch_autotune: returns ({"k_shared", "threads_shared", "k_global",
+    "threads_global"}, {(class, k, threads): ms}) with class "shared" (n <= 14)
+    or "global"."""
     lib = load()
     n = len(circuits)
     hs = (C.c_void_p * n)(*[c.h for c in circuits])
-    bk, bt = C.c_uint32(), C.c_uint32()
-    table = np.zeros((kmax - kmin + 1) * 3)
+    best = qt_batch_tuning()
+    nk = kmax - kmin + 1
+    table = np.zeros(2 * nk * 3)
     _check(lib.qt_batch_autotune(n, C.cast(hs, C.c_void_p), sample, kmin, kmax, stream,
-                                 C.byref(bk), C.byref(bt), _ptr(table)))
+                                 C.byref(best), _ptr(table)))
     res = {}
-    for k in range(kmin, kmax + 1):
-        for ti, th in enumerate((128, 256, 512)):
-            res[(k, th)] = float(table[(k - kmin) * 3 + ti])
-    return bk.value, bt.value, res
+    for ci, cls in enumerate(("shared", "global")):
+        for k in range(kmin, kmax + 1):
+            for ti, th in enumerate((128, 256, 512)):
+                res[(cls, k, th)] = float(table[(ci * nk + k - kmin) * 3 + ti])
+    return {f: getattr(best, f) for f, _ in qt_batch_tuning._fields_}, res
+
+
+def fuse_by_class(circuits, tuning, threads=0):
+    """Fuse each circuit at its class's width from autotune_batch (shared-memory
+    states n <= 14: k_shared; larger: k_global); returns Fused handles in order."""
+    out = [None] * len(circuits)
+    for cls, k in (("shared", tuning["k_shared"]), ("global", tuning["k_global"])):
+        idx = [i for i, c in enumerate(circuits) if (c.num_qubits > SMEM_N_MAX) == (cls == "global")]
+        if idx:
+            for i, f in zip(idx, fuse_many([circuits[i] for i in idx], k, threads)):
+                out[i] = f
+    return out
 
 
 # ----------------------------------------------------------------------------

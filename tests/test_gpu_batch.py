@@ -41,11 +41,12 @@ def _noisy(n, depth, seed, gamma):
                               dep1=0.02, dep2=0.02, per_gate_ad=gamma)
 
 
-def check_batch(qt, orc, ccs, k, *, seed=0, first=0, S=100, threads=0):
+def check_batch(qt, orc, ccs, k, *, seed=0, first=0, S=100, threads=0, threads_global=0):
+    """k: one fusion width, or a tuning dict of per-class widths (fuse_by_class)."""
     qcs = [qt.Circuit.from_compact(c) for c in ccs]
-    fs = qt.fuse_many(qcs, k)
+    fs = qt.fuse_by_class(qcs, k) if isinstance(k, dict) else qt.fuse_many(qcs, k)
     b = qt.Batch(fs).run(seed=seed, first_traj=first, samples_per_traj=S, keep_states=True,
-                         threads=threads)
+                         threads=threads, threads_global=threads_global)
     smp = b.samples()
     compared = 0
     for i, cc in enumerate(ccs):
@@ -85,13 +86,25 @@ def test_batch_forced_flushes(qt, orc, k):
     assert b.stats()["flushes"] > 0
 
 
-@pytest.mark.parametrize("k", [2, 3])
-def test_batch_global_memory_states_match_oracle(qt, orc, k):
-    """States of 2^15..2^18 amplitudes (a CTA's slot of global memory, 16 loads in flight per
-    thread) next to shared-memory states, with forced stage-2 flushes."""
+@pytest.mark.parametrize("k,tg", [(1, 512), (2, 256), (3, 512), (4, 128), (5, 256), (6, 512)])
+def test_batch_global_memory_states_match_oracle(qt, orc, k, tg):
+    """States of 2^15..2^18 amplitudes (a CTA's slot of global memory, up to 32 loads in
+    flight per thread, packed FMAs) next to shared-memory states in the second launch,
+    with forced stage-2 flushes, at every fusion width and several CTA sizes."""
     ccs = [_noisy(n, 6, s, 0.08) for s, n in enumerate([15, 16, 17, 18, 9, 12])]
-    b, _ = check_batch(qt, orc, ccs, k, seed=5, first=300, S=64, threads=512)
+    b, _ = check_batch(qt, orc, ccs, k, seed=5, first=300, S=64, threads=512, threads_global=tg)
     assert b.stats()["flushes"] > 0
+
+
+def test_batch_per_class_widths_match_oracle(qt, orc):
+    """Shared-memory states fused to k = 2 and global-memory states to k = 4 in one
+    batch (the autotuner's per-class choice), against the oracle."""
+    ccs = [_noisy(n, 8, s, 0.05) for s, n in enumerate([8, 11, 14, 15, 17, 18, 10, 16])]
+    tune = {"k_shared": 2, "threads_shared": 256, "k_global": 4, "threads_global": 512}
+    b, fs = check_batch(qt, orc, ccs, tune, seed=8, first=500, S=64, threads=256, threads_global=512)
+    widths = [f.info()["max_width"] for f in fs]
+    assert max(w for w, c in zip(widths, ccs) if c.num_qubits <= 14) <= 2
+    assert max(w for w, c in zip(widths, ccs) if c.num_qubits > 14) == 4
 
 
 def test_batch_equals_plain_loop(qt):
@@ -127,8 +140,11 @@ def test_batch_graph_replay(qt):
 def test_batch_autotuner(qt):
     ccs = _workload_circuits(max_n=18, count=48)
     qcs = [qt.Circuit.from_compact(c) for c in ccs]
-    k, threads, table = qt.autotune_batch(qcs, sample=24, kmin=2, kmax=6)
-    assert k in (2, 3, 4, 5, 6) and threads in (128, 256, 512)
-    assert len(table) == 15
-    assert all(v > 0 for v in table.values())
-    assert table[(k, threads)] == min(table.values())
+    tune, table = qt.autotune_batch(qcs, sample=24, kmin=2, kmax=6)
+    assert len(table) == 30
+    for cls in ("shared", "global"):
+        k, threads = tune[f"k_{cls}"], tune[f"threads_{cls}"]
+        assert k in (2, 3, 4, 5, 6) and threads in (128, 256, 512)
+        mine = {key: v for key, v in table.items() if key[0] == cls}
+        assert all(v > 0 for v in mine.values())
+        assert table[(cls, k, threads)] == min(mine.values())
