@@ -529,9 +529,9 @@ SERVE_WORKLOAD = ("serve: requests with n ~ U{10..28}, depth ~ U{10..30}, chain 
                   "trajectory, Poisson arrivals at 0.9x the plain loop's service rate, 150 GB HBM budget")
 
 
-def serve_stream(pkg, fused, reqs, arrivals, *, slots, small_n_max, budget, keep=()):
+def serve_stream(pkg, fused, reqs, arrivals, *, slots, small_n_max, budget, keep=(), share_prefix=True):
     """Serve the stream; keep: request indices whose samples are returned."""
-    srv = pkg.Server(budget, max_slots=slots, small_n_max=small_n_max)
+    srv = pkg.Server(budget, max_slots=slots, small_n_max=small_n_max, share_prefix=share_prefix)
     ids = [None] * len(reqs)
     t0 = time.perf_counter()
 
@@ -582,8 +582,11 @@ def served_form(requests=160, slots=8, uuid=None):
     clk = ClockSampler(uuid)
     torch.cuda.synchronize()
     clk.start()
-    # calibration = the plain loop's burst: the whole stream request by request
-    lat_c, t_cal, _, _, _ = serve_stream(pkg, fused, reqs, [0.0] * R, slots=1, small_n_max=0, budget=budget)
+    # calibration = the plain loop's burst: the whole stream request by request,
+    # every trajectory on its own
+    plain = dict(slots=1, small_n_max=0, budget=budget, share_prefix=False)
+    served = dict(slots=slots, small_n_max=20, budget=budget)
+    lat_c, t_cal, _, _, _ = serve_stream(pkg, fused, reqs, [0.0] * R, **plain)
     rate = 0.9 * R / t_cal
     rng = np.random.default_rng(1234)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, R)).tolist()
@@ -591,10 +594,12 @@ def served_form(requests=160, slots=8, uuid=None):
     total_traj = sum(r["num_traj"] for r in reqs)
     # oracle parity on a seeded subsample: every 25th request with n <= 20, its first trajectory
     sub = [k for k in range(0, R, 25) if reqs[k]["n"] <= 20]
-    lat_s, t_s, st_s, nb, kept = serve_stream(pkg, fused, reqs, arrivals, slots=slots, small_n_max=20,
-                                              budget=budget, keep=sub)
-    lat_p, t_p, _, _, _ = serve_stream(pkg, fused, reqs, arrivals, slots=1, small_n_max=0, budget=budget)
-    lat_b, t_b, _, _, _ = serve_stream(pkg, fused, reqs, [0.0] * R, slots=slots, small_n_max=20, budget=budget)
+    lat_s, t_s, st_s, nb, kept = serve_stream(pkg, fused, reqs, arrivals, keep=sub, **served)
+    lat_p, t_p, _, _, _ = serve_stream(pkg, fused, reqs, arrivals, **plain)
+    lat_b, t_b, st_b, _, _ = serve_stream(pkg, fused, reqs, [0.0] * R, **served)
+    # the same served burst with the plain workers' trajectories run one by one
+    # (merged launches and concurrency only, no shared prefixes)
+    lat_n, t_n, _, _, _ = serve_stream(pkg, fused, reqs, [0.0] * R, share_prefix=False, **served)
     clocks = clk.stop()
     compared = mismatched = 0
     for k in sub:
@@ -611,13 +616,18 @@ def served_form(requests=160, slots=8, uuid=None):
         "batched_requests": "n <= 14, or n <= 20 with >= 64 trajectories",
         "poisson": {"served": {"traj_per_s": total_traj / t_s, "p50_s": pct(lat_s, 50), "p99_s": pct(lat_s, 99),
                                "makespan_s": t_s, "peak_inflight_bytes": st_s["peak_inflight_bytes"],
-                               "requests_batched": nb},
+                               "requests_batched": nb, "lane_launches": st_s["lane_launches"]},
                     "plain_request_by_request": {"traj_per_s": total_traj / t_p, "p50_s": pct(lat_p, 50),
                                                  "p99_s": pct(lat_p, 99), "makespan_s": t_p}},
         "burst": {"served_traj_per_s": total_traj / t_b, "plain_traj_per_s": total_traj / t_cal,
                   "served_p50_s": pct(lat_b, 50), "served_p99_s": pct(lat_b, 99),
                   "plain_p50_s": pct(lat_c, 50), "plain_p99_s": pct(lat_c, 99),
-                  "capacity_ratio": t_cal / t_b},
+                  "capacity_ratio": t_cal / t_b, "lane_launches": st_b["lane_launches"],
+                  "served_without_shared_prefix": {"traj_per_s": total_traj / t_n, "p50_s": pct(lat_n, 50),
+                                                   "p99_s": pct(lat_n, 99), "capacity_ratio": t_cal / t_n}},
+        "forms": {"served": "batch lane (small requests merged into shared launches of the batched kernel) + "
+                            f"{slots} plain workers whose requests share their trajectories' default-choice prefix",
+                  "plain_request_by_request": "one worker, the plain per-trajectory loop, no lane, no sharing"},
         "parity": {"requests": sub, "samples_compared": compared, "sample_mismatches": mismatched,
                    "note": "first trajectory of every 25th request with n <= 20 against the FP64 oracle; "
                            "samples whose CDF margin is <= 1e-6 are ties and not compared"},

@@ -349,12 +349,15 @@ qt_status qt_batch_autotune(uint32_t num, const qt_circuit* const* circuits, uin
 /* ---------------------------------------------------------------------- */
 typedef struct {
   uint64_t budget_bytes;       /* device-memory budget for resident states */
-  uint32_t max_slots;          /* concurrent requests (one stream each), 1..64 */
-  uint32_t small_n_max;        /* batched form for n <= 14, and for n <= this (<= 20) when a
-                                  request has >= 64 trajectories (0: never batched) */
-  uint32_t flags;              /* QT_SERVER_DRY_RUN: no GPU work (scheduling only) */
+  uint32_t max_slots;          /* concurrent plain-loop requests (one stream each), 1..64 */
+  uint32_t small_n_max;        /* the batch lane takes requests of n <= 14, and of n <= this
+                                  (<= 20) when a request has >= 64 trajectories; 0: no lane */
+  uint32_t flags;              /* QT_SERVER_DRY_RUN: no GPU work (scheduling only);
+                                  QT_SERVER_NO_SHARED_PREFIX: plain workers run every
+                                  trajectory on its own (the per-trajectory loop) */
 } qt_server_config;
 #define QT_SERVER_DRY_RUN 1u
+#define QT_SERVER_NO_SHARED_PREFIX 2u
 
 typedef struct {
   uint64_t seed;               /* Philox key */
@@ -377,16 +380,35 @@ typedef struct {
 } qt_server_req_info;
 
 typedef struct {
-  uint64_t budget, inflight_bytes, peak_inflight_bytes;
+  uint64_t budget, inflight_bytes, peak_inflight_bytes;   /* in-flight bytes include the lane's */
   uint32_t queued, running, done, failed, workers_alive, requeued, deferred, pad;
+  uint64_t lane_bytes;         /* reserved for the batch lane's global-memory state slots */
+  uint64_t lane_launches;      /* merged launches of the batch lane */
+  uint64_t lane_trajectories;  /* trajectories they ran */
 } qt_server_stats_t;
 
 enum { QT_FAULT_WORKER_EXIT = 1, QT_FAULT_ALLOC = 2 };
 
-/* Start max_slots workers, each with its own CUDA stream on the current
- * device.  A request is admitted in arrival order as soon as a worker is free
- * and the footprint of the requests in flight plus its own (8 * 2^n bytes per
- * resident state, Sec. IV.A) fits budget_bytes. */
+/* Start the server on the current device: max_slots plain-loop workers,
+ * each with its own CUDA stream, and (small_n_max > 0) a batch lane with a
+ * stream of its own.
+ *   - Batch lane: small requests (see small_n_max; ops on <= 2 qubits) wait in
+ *     their own queue; whenever the lane is free it takes all of them at once
+ *     and runs their trajectories -- each with its own circuit, seed and
+ *     trajectory id -- in one merged launch of the batched kernel (the
+ *     trajectories-as-independent-jobs workload of Sec. IV); requests arriving
+ *     meanwhile join the next launch.  Its global-memory state slots (one per
+ *     SM, 8 * 2^small_n_max bytes each, for n > 14) are reserved against the
+ *     budget at creation (the lane keeps to n <= 14 if they would take more
+ *     than half the budget).
+ *   - Plain workers: the other requests are admitted in arrival order as soon
+ *     as a worker is free and the footprint of the requests in flight plus
+ *     its own fits budget_bytes: 8 * 2^n bytes per resident state (Sec. IV.A),
+ *     two states when the request has more than one trajectory (they share
+ *     the default-choice prefix, QT_FLAG_SHARE_PREFIX, unless the server was
+ *     created with QT_SERVER_NO_SHARED_PREFIX), plus scratch.
+ * A request's results depend only on its own circuit, seed and trajectory
+ * ids, so they are the same alone and in any mix. */
 qt_status qt_server_create(const qt_server_config* cfg, qt_server** out);
 /* Queue a request; the fused circuit must outlive it.  A request whose
  * footprint alone exceeds the budget is refused (QT_ERR_OUT_OF_MEMORY). */
@@ -402,10 +424,11 @@ qt_status qt_server_result(qt_server* s, uint64_t id, uint64_t* samples, size_t 
 /* Forget a finished request. */
 qt_status qt_server_release(qt_server* s, uint64_t id);
 qt_status qt_server_stats(qt_server* s, qt_server_stats_t* out);
-/* Host-side fault injection: the next `count` dequeues kill their worker
- * thread (QT_FAULT_WORKER_EXIT; the watchdog requeues the request and starts
- * a replacement worker) or fail with an allocation error (QT_FAULT_ALLOC;
- * the request is deferred and retried). */
+/* Host-side fault injection: the next `count` dequeues (by a worker or the
+ * lane) kill their thread (QT_FAULT_WORKER_EXIT; the watchdog requeues the
+ * request -- every request of the lane's launch -- and starts a replacement)
+ * or fail with an allocation error (QT_FAULT_ALLOC; the requests are deferred
+ * and retried). */
 qt_status qt_server_inject(qt_server* s, uint32_t fault, uint32_t count);
 /* Finish running requests, stop the workers and free the server. */
 void qt_server_destroy(qt_server* s);
@@ -422,10 +445,10 @@ void qt_server_destroy(qt_server* s);
  * QT_ERR_UNSUPPORTED and a message naming the limit).  Every call looks up
  * that array's device address in the current context (so a device reset does
  * not leave a stale address behind); the first call on a device may load the
- * library's module there, so make that first call before any stream capture.  All calls share the array and
- * it keeps the last call's contents (nothing in it needs to start at zero),
- * so calls whose kernels overlap on the GPU -- different streams or host
- * threads -- race: order them. */
+ * library's module there, so make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents
+ * (nothing in it needs to start at zero), so calls whose kernels overlap on
+ * the GPU -- different streams or host threads -- race: order them. */
 qt_status qt_state_reduced_density_noalloc(const void* state, uint32_t n, uint32_t q,
                                            const uint32_t* qubits, double* out, void* stream);
 

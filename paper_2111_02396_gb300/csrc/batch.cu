@@ -49,7 +49,10 @@ constexpr int kMaxN = 20;           // widest state of the batched form
 struct Traj {
   uint32_t n, gate0, ngates, op0, nops, ch0, nch, chop0;   // ch0: output offset; chop0: ch_op table offset
   uint64_t arena_off;               // amplitude offset of the kept state (keep_states)
-  uint32_t gf0, pad;                // offset of this trajectory's per-gate flags (per trajectory, like ch0)
+  uint32_t gf0, S;                  // offset of this trajectory's per-gate flags (per trajectory, like ch0);
+                                    // with per-trajectory parameters: its sample count
+  uint64_t seed, tid, soff;         // with per-trajectory parameters: Philox key, trajectory id, first
+                                    // sample slot (a merged launch over several requests)
 };
 struct Op {
   uint8_t kind, q, q0, q1;
@@ -87,6 +90,7 @@ struct Dev {
   int* err;
   const uint64_t* run;              // {seed, first_traj} of the current run (device copy)
   uint32_t num, S, keep;
+  uint32_t per_traj;                // 1: seed, id and samples from each Traj (merged launches)
 };
 
 // ---------------------------------------------------------------------------
@@ -512,8 +516,10 @@ __global__ void __launch_bounds__(512) k_batch(const __grid_constant__ Dev d) {
     const Traj T = d.traj[ti];
     const int n = static_cast<int>(T.n);
     const uint64_t amps = 1ull << n;
-    const uint64_t seed = d.run[0];
-    const uint64_t traj_id = d.run[1] + ti;
+    const uint64_t seed = d.per_traj ? T.seed : d.run[0];
+    const uint64_t traj_id = d.per_traj ? T.tid : d.run[1] + ti;
+    const uint32_t S = d.per_traj ? T.S : d.S;
+    uint64_t* samples = d.samples + (d.per_traj ? T.soff : static_cast<uint64_t>(ti) * d.S);
     float2* psi;
     if (!GLOBAL) psi = s_state;
     else psi = d.keep ? d.arena + T.arena_off : d.arena + static_cast<uint64_t>(blockIdx.x) * d.slot_amps;
@@ -673,7 +679,7 @@ __global__ void __launch_bounds__(512) k_batch(const __grid_constant__ Dev d) {
       }
     }
     __syncthreads();
-    if (d.S) cta_sample(psi, n, seed, traj_id, d.S, d.samples + static_cast<uint64_t>(ti) * d.S, s_wcum);
+    if (S) cta_sample(psi, n, seed, traj_id, S, samples, s_wcum);
     if (d.keep && !GLOBAL) {
       __syncthreads();
       for (uint64_t x = tid; x < amps; x += blockDim.x) d.arena[T.arena_off + x] = psi[x];
@@ -750,6 +756,8 @@ struct qt_batch {
   size_t off_kraus = 0, off_stage = 0, off_samples = 0, off_flushes = 0, off_err = 0, off_gflag = 0;
   uint64_t total_gates = 0;         // sum of the trajectories' fused-gate counts (one flag each per run)
   uint32_t S = 0, keep = 0;
+  std::vector<uint8_t> host;        // host image of the device tables
+  uint64_t lane_samples = 0;        // merged launches: total sample slots
   qt_batch_params last{};
   // results on the host
   std::vector<int32_t> kraus, stage;
@@ -776,6 +784,271 @@ struct qt_batch {
     if (side) cudaStreamDestroy(side);
   }
 };
+
+// Pack num fused circuits (trajectory i runs fused[i]) into B's host fields
+// and device tables: B->tables grows when the image does not fit, and the
+// image is copied with cudaMemcpyAsync on st (the call returns once the
+// pageable source has been staged).  per (optional): per-trajectory seed,
+// trajectory id and sample count of a merged launch.
+static qt_status pack_batch(qt_batch* B, uint32_t num, const qt_fused* const* fused, const LaneTraj* per,
+                            const char* who, cudaStream_t st) {
+  B->num = num;
+  B->total_ch = 0;
+  B->total_amps = 0;
+  B->max_n = 0;
+  B->nglob = 0;
+  B->total_gates = 0;
+  B->gate_ops = 0;
+  B->fused_gates = 0;
+  B->traj.assign(num, bt::Traj{});
+  // ---- per-circuit checks and distinct operator sets ----
+  std::unordered_map<uint64_t, std::vector<uint32_t>> set_index;
+  std::vector<const Op*> sets;
+  std::vector<bt::Op> ops;
+  std::vector<bt::Gate> gates;
+  std::vector<uint32_t> members, ch_op;
+  std::vector<float2> fmat;
+  std::vector<double> dmat;
+  std::vector<uint32_t> set_fmat, set_kraus, set_mtm, set_pbar;
+  // a fused circuit that appears several times (e.g. many trajectories of one
+  // request) is packed once; its trajectories share the tables
+  std::unordered_map<const qt_fused*, uint32_t> first_use;
+  for (uint32_t i = 0; i < num; ++i) {
+    const qt_fused* f = fused[i];
+    if (!f) return set_error(QT_ERR_INVALID_ARG, "%s: fused %u is NULL", who, i);
+    auto seen = first_use.find(f);
+    if (seen != first_use.end()) {
+      const bt::Traj& P = B->traj[seen->second];
+      bt::Traj& T = B->traj[i];
+      T = P;
+      T.ch0 = B->total_ch;                 // outputs and per-run flags are per trajectory
+      B->total_ch += T.nch;
+      T.gf0 = static_cast<uint32_t>(B->total_gates);
+      B->total_gates += T.ngates;
+      B->gate_ops += f->gate_ops;
+      continue;
+    }
+    first_use.emplace(f, i);
+    const Circuit& c = *f->c;
+    if (c.n > static_cast<uint32_t>(bt::kMaxN) || c.n < 1)
+      return set_error(QT_ERR_UNSUPPORTED, "%s: circuit %u has %u qubits (batched form: 1..%d)", who, i, c.n,
+                       bt::kMaxN);
+    bt::Traj& T = B->traj[i];
+    T.n = c.n;
+    T.op0 = static_cast<uint32_t>(ops.size());
+    T.nops = static_cast<uint32_t>(c.ops.size());
+    T.ch0 = B->total_ch;
+    T.chop0 = static_cast<uint32_t>(ch_op.size());
+    T.nch = static_cast<uint32_t>(c.channel_op.size());
+    T.gate0 = static_cast<uint32_t>(gates.size());
+    T.ngates = static_cast<uint32_t>(f->gates.size());
+    T.gf0 = static_cast<uint32_t>(B->total_gates);
+    B->total_gates += T.ngates;
+    B->total_ch += T.nch;
+    B->max_n = std::max(B->max_n, c.n);
+    std::vector<uint32_t> local_sets;   // set ids by op
+    // within-circuit cache: consecutive ops mostly repeat a handful of sets
+    std::vector<std::pair<const Op*, uint32_t>> recent;
+    for (uint32_t oi = 0; oi < c.ops.size(); ++oi) {
+      const Op& op = c.ops[oi];
+      if (op.q > 2) return set_error(QT_ERR_UNSUPPORTED, "%s: circuit %u op %u has %u qubits (batched form: <= 2)", who, i, oi, op.q);
+      uint32_t sid = UINT32_MAX;
+      for (auto& r : recent)
+        if (same_set(*r.first, op)) { sid = r.second; break; }
+      if (sid == UINT32_MAX) {
+        const uint64_t h = set_hash(op);
+        auto& bucket = set_index[h];
+        for (uint32_t cand : bucket)
+          if (same_set(*sets[cand], op)) { sid = cand; break; }
+        if (sid == UINT32_MAX) {
+          sid = static_cast<uint32_t>(sets.size());
+          sets.push_back(&op);
+          bucket.push_back(sid);
+        }
+        recent.emplace_back(&op, sid);
+        if (recent.size() > 16) recent.erase(recent.begin());
+      }
+      bt::Op o{};
+      o.kind = static_cast<uint8_t>(op.kind);
+      o.q = static_cast<uint8_t>(op.q);
+      o.q0 = static_cast<uint8_t>(op.qubits[0]);
+      o.q1 = static_cast<uint8_t>(op.q > 1 ? op.qubits[1] : 0);
+      o.set = sid;
+      o.channel = op.channel;
+      ops.push_back(o);
+      if (op.channel >= 0) ch_op.push_back(oi);
+      if (op.kind == QT_OP_GATE) B->gate_ops++;
+    }
+    for (const FusedGate& fg : f->gates) {
+      if (fg.targets.size() > static_cast<size_t>(bt::kMaxW))
+        return set_error(QT_ERR_UNSUPPORTED, "%s: fused width %zu > %d in circuit %u", who, fg.targets.size(),
+                         bt::kMaxW, i);
+      bt::Gate g{};
+      g.w = static_cast<uint8_t>(fg.targets.size());
+      for (size_t b = 0; b < fg.targets.size(); ++b) g.t[b] = static_cast<uint8_t>(fg.targets[b]);
+      g.mat = static_cast<uint32_t>(fmat.size());
+      for (const cd& x : fg.def) fmat.push_back(make_float2(static_cast<float>(x.real()), static_cast<float>(x.imag())));
+      g.mem0 = static_cast<uint32_t>(members.size());
+      g.nmem = static_cast<uint32_t>(fg.members.size());
+      g.minpos = UINT32_MAX;
+      g.maxpos = 0;
+      for (uint32_t m : fg.members) {
+        members.push_back(m);
+        g.minpos = std::min(g.minpos, m);
+        g.maxpos = std::max(g.maxpos, m);
+      }
+      gates.push_back(g);
+      B->fused_gates++;
+    }
+    if (fmat.size() > 0x7fffffffu) return set_error(QT_ERR_UNSUPPORTED, "%s: matrix table too large", who);
+  }
+  // operator-set tables
+  std::vector<bt::Set> dsets(sets.size());
+  for (size_t s = 0; s < sets.size(); ++s) {
+    const Op& op = *sets[s];
+    bt::Set& S = dsets[s];
+    S.nk = op.num_ops;
+    S.q = op.q;
+    S.def = static_cast<uint32_t>(op.def);
+    S.mat = static_cast<uint32_t>(fmat.size());
+    for (const cd& x : op.mats) fmat.push_back(make_float2(static_cast<float>(x.real()), static_cast<float>(x.imag())));
+    S.kraus = static_cast<uint32_t>(fmat.size());
+    const std::vector<cd>& kr = op.kind == QT_OP_GATE ? op.mats : op.kraus;
+    for (const cd& x : kr) fmat.push_back(make_float2(static_cast<float>(x.real()), static_cast<float>(x.imag())));
+    S.mtm = static_cast<uint32_t>(dmat.size());
+    for (const cd& x : op.mtm) { dmat.push_back(x.real()); dmat.push_back(x.imag()); }
+    S.pbar = static_cast<uint32_t>(dmat.size());
+    for (double p : op.pbar) dmat.push_back(p);
+    if (op.pbar.empty()) dmat.push_back(0.0);
+  }
+  // processing order: largest states first
+  B->order.resize(num);
+  for (uint32_t i = 0; i < num; ++i) B->order[i] = i;
+  std::stable_sort(B->order.begin(), B->order.end(),
+                   [&](uint32_t a, uint32_t b) { return B->traj[a].n > B->traj[b].n; });
+  uint64_t soff = 0;
+  for (uint32_t i = 0; i < num; ++i) {
+    bt::Traj& T = B->traj[i];
+    T.arena_off = B->total_amps;
+    B->total_amps += 1ull << T.n;
+    if (T.n > static_cast<uint32_t>(bt::kSmemNMax)) B->nglob++;
+    T.seed = per ? per[i].seed : 0;
+    T.tid = per ? per[i].traj : 0;
+    T.S = per ? per[i].S : 0;
+    T.soff = soff;
+    soff += T.S;
+  }
+  B->lane_samples = soff;
+  // ---- one device buffer for all tables ----
+  auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
+  size_t off = 0;
+  const size_t o_traj = off; off = align(off + sizeof(bt::Traj) * num);
+  const size_t o_ops = off; off = align(off + sizeof(bt::Op) * ops.size());
+  const size_t o_sets = off; off = align(off + sizeof(bt::Set) * dsets.size());
+  const size_t o_gates = off; off = align(off + sizeof(bt::Gate) * std::max<size_t>(gates.size(), 1));
+  const size_t o_mem = off; off = align(off + sizeof(uint32_t) * std::max<size_t>(members.size(), 1));
+  const size_t o_chop = off; off = align(off + sizeof(uint32_t) * std::max<size_t>(ch_op.size(), 1));
+  const size_t o_fmat = off; off = align(off + sizeof(float2) * fmat.size());
+  const size_t o_dmat = off; off = align(off + sizeof(double) * std::max<size_t>(dmat.size(), 1));
+  const size_t o_order = off; off = align(off + sizeof(uint32_t) * num);
+  if (B->tables.bytes < off && !B->tables.alloc(off))
+    return set_error(QT_ERR_OUT_OF_MEMORY, "%s: device tables (%zu bytes)", who, off);
+  std::vector<uint8_t>& host = B->host;
+  host.assign(off, 0);
+  auto put = [&](size_t o, const void* src, size_t n) { if (n) std::memcpy(host.data() + o, src, n); };
+  put(o_traj, B->traj.data(), sizeof(bt::Traj) * num);
+  put(o_ops, ops.data(), sizeof(bt::Op) * ops.size());
+  put(o_sets, dsets.data(), sizeof(bt::Set) * dsets.size());
+  put(o_gates, gates.data(), sizeof(bt::Gate) * gates.size());
+  put(o_mem, members.data(), sizeof(uint32_t) * members.size());
+  put(o_chop, ch_op.data(), sizeof(uint32_t) * ch_op.size());
+  put(o_fmat, fmat.data(), sizeof(float2) * fmat.size());
+  put(o_dmat, dmat.data(), sizeof(double) * dmat.size());
+  put(o_order, B->order.data(), sizeof(uint32_t) * num);
+  cudaError_t e = cudaMemcpyAsync(B->tables.p, host.data(), off, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return set_error(QT_ERR_CUDA, "%s: cudaMemcpyAsync: %s", who, cudaGetErrorString(e));
+  uint8_t* base = static_cast<uint8_t*>(B->tables.p);
+  bt::Dev& d = B->dev;
+  d.traj = reinterpret_cast<const bt::Traj*>(base + o_traj);
+  d.ops = reinterpret_cast<const bt::Op*>(base + o_ops);
+  d.sets = reinterpret_cast<const bt::Set*>(base + o_sets);
+  d.gates = reinterpret_cast<const bt::Gate*>(base + o_gates);
+  d.members = reinterpret_cast<const uint32_t*>(base + o_mem);
+  d.ch_op = reinterpret_cast<const uint32_t*>(base + o_chop);
+  d.fmat = reinterpret_cast<const float2*>(base + o_fmat);
+  d.dmat = reinterpret_cast<const double*>(base + o_dmat);
+  d.order = reinterpret_cast<const uint32_t*>(base + o_order);
+  d.num = num;
+  return QT_OK;
+}
+
+// counters, pinned run parameters, and the side stream of the second launch
+static qt_status init_batch_runtime(qt_batch* B, const char* who) {
+  bt::Dev& d = B->dev;
+  // work counters of the two launches (2 x 4 B), error flag (4 B), run parameters at +16 (2 x 8 B)
+  if (!B->counter.alloc(32)) return set_error(QT_ERR_OUT_OF_MEMORY, "%s: counter", who);
+  d.counter = static_cast<unsigned int*>(B->counter.p);
+  d.err = reinterpret_cast<int*>(static_cast<unsigned int*>(B->counter.p) + 2);
+  d.run = reinterpret_cast<const uint64_t*>(static_cast<uint8_t*>(B->counter.p) + 16);
+  if (cudaMallocHost(&B->hrun, 2 * sizeof(uint64_t)) != cudaSuccess)
+    return set_error(QT_ERR_OUT_OF_MEMORY, "%s: pinned parameters", who);
+  if (cudaStreamCreateWithFlags(&B->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&B->ev_join, cudaEventDisableTiming) != cudaSuccess)
+    return set_error(QT_ERR_CUDA, "%s: side stream", who);
+  return QT_OK;
+}
+
+// dynamic shared memory of the two launches: the matrix area (64 x 64
+// complex64) and, for global states, its 16 x 16 (x, x, y, y) expansion
+// behind it; the shared-memory class adds the 2^14-amplitude state
+constexpr size_t kSmemMat = sizeof(float2) * (1u << (2 * bt::kMaxW)) + sizeof(float4) * 256;
+constexpr size_t kSmemState = (sizeof(float2) << bt::kSmemNMax) + kSmemMat;
+
+static cudaError_t batch_kernel_attrs() {
+  static PerDevice attr_set;
+  return static_cast<cudaError_t>(attr_set.get([] {
+    cudaError_t e1 = cudaFuncSetAttribute(bt::k_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          static_cast<int>(kSmemState));
+    if (e1 == cudaSuccess)
+      e1 = cudaFuncSetAttribute(bt::k_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(kSmemMat));
+    return static_cast<int>(e1);
+  }));
+}
+
+// One run's two persistent launches on stream s, with tables, outputs and
+// arena as d holds them: the work counters are zeroed, the global-memory
+// class launches on s and the shared-memory class on the side stream (forked
+// from and joined back into s), so that its CTAs take SMs as the first
+// launch's CTAs retire.
+static cudaError_t launch_classes(qt_batch* b, const bt::Dev& d, uint32_t threads, uint32_t threads_glob,
+                                  cudaStream_t s) {
+  const uint32_t nglob = b->nglob, nsh = b->num - b->nglob;
+  const unsigned grid_g = static_cast<unsigned>(std::min<uint64_t>(sm_count(), nglob));
+  const unsigned grid_s = static_cast<unsigned>(std::min<uint64_t>(sm_count(), nsh));
+  bt::Dev dg = d, ds = d;
+  dg.num = nglob;
+  ds.order = d.order + nglob;
+  ds.num = nsh;
+  ds.counter = d.counter + 1;
+  cudaError_t r = cudaMemsetAsync(b->counter.p, 0, 2 * sizeof(unsigned int) + sizeof(int), s);
+  if (r != cudaSuccess) return r;
+  const bool both = nglob && nsh;
+  if (both) {
+    r = cudaEventRecord(b->ev_fork, s);
+    if (r == cudaSuccess) r = cudaStreamWaitEvent(b->side, b->ev_fork, 0);
+    if (r != cudaSuccess) return r;
+  }
+  if (nglob) bt::k_batch<true><<<grid_g, threads_glob, kSmemMat, s>>>(dg);
+  if (nsh) bt::k_batch<false><<<grid_s, threads, kSmemState, both ? b->side : s>>>(ds);
+  r = cudaGetLastError();
+  if (r == cudaSuccess && both) {
+    r = cudaEventRecord(b->ev_join, b->side);
+    if (r == cudaSuccess) r = cudaStreamWaitEvent(s, b->ev_join, 0);
+  }
+  return r;
+}
 
 extern "C" {
 
@@ -826,187 +1099,11 @@ qt_status qt_batch_create(uint32_t num, const qt_fused* const* fused, qt_batch**
   *out = nullptr;
   std::unique_ptr<qt_batch> B(new (std::nothrow) qt_batch());
   if (!B) return set_error(QT_ERR_OUT_OF_MEMORY, "qt_batch_create: host allocation");
-  B->num = num;
-  // ---- per-circuit checks and distinct operator sets ----
-  std::unordered_map<uint64_t, std::vector<uint32_t>> set_index;
-  std::vector<const Op*> sets;
-  std::vector<bt::Op> ops;
-  std::vector<bt::Gate> gates;
-  std::vector<uint32_t> members, ch_op;
-  std::vector<float2> fmat;
-  std::vector<double> dmat;
-  std::vector<uint32_t> set_fmat, set_kraus, set_mtm, set_pbar;
-  B->traj.resize(num);
-  // a fused circuit that appears several times (e.g. many trajectories of one
-  // request) is packed once; its trajectories share the tables
-  std::unordered_map<const qt_fused*, uint32_t> first_use;
-  for (uint32_t i = 0; i < num; ++i) {
-    const qt_fused* f = fused[i];
-    if (!f) return set_error(QT_ERR_INVALID_ARG, "qt_batch_create: fused %u is NULL", i);
-    auto seen = first_use.find(f);
-    if (seen != first_use.end()) {
-      const bt::Traj& P = B->traj[seen->second];
-      bt::Traj& T = B->traj[i];
-      T = P;
-      T.ch0 = B->total_ch;                 // outputs and per-run flags are per trajectory
-      B->total_ch += T.nch;
-      T.gf0 = static_cast<uint32_t>(B->total_gates);
-      B->total_gates += T.ngates;
-      B->gate_ops += f->gate_ops;
-      continue;
-    }
-    first_use.emplace(f, i);
-    const Circuit& c = *f->c;
-    if (c.n > static_cast<uint32_t>(bt::kMaxN) || c.n < 1)
-      return set_error(QT_ERR_UNSUPPORTED, "qt_batch_create: circuit %u has %u qubits (batched form: 1..%d)", i, c.n,
-                       bt::kMaxN);
-    bt::Traj& T = B->traj[i];
-    T.n = c.n;
-    T.op0 = static_cast<uint32_t>(ops.size());
-    T.nops = static_cast<uint32_t>(c.ops.size());
-    T.ch0 = B->total_ch;
-    T.chop0 = static_cast<uint32_t>(ch_op.size());
-    T.nch = static_cast<uint32_t>(c.channel_op.size());
-    T.gate0 = static_cast<uint32_t>(gates.size());
-    T.ngates = static_cast<uint32_t>(f->gates.size());
-    T.gf0 = static_cast<uint32_t>(B->total_gates);
-    B->total_gates += T.ngates;
-    B->total_ch += T.nch;
-    B->max_n = std::max(B->max_n, c.n);
-    std::vector<uint32_t> local_sets;   // set ids by op
-    // within-circuit cache: consecutive ops mostly repeat a handful of sets
-    std::vector<std::pair<const Op*, uint32_t>> recent;
-    for (uint32_t oi = 0; oi < c.ops.size(); ++oi) {
-      const Op& op = c.ops[oi];
-      if (op.q > 2) return set_error(QT_ERR_UNSUPPORTED, "qt_batch_create: circuit %u op %u has %u qubits (batched form: <= 2)", i, oi, op.q);
-      uint32_t sid = UINT32_MAX;
-      for (auto& r : recent)
-        if (same_set(*r.first, op)) { sid = r.second; break; }
-      if (sid == UINT32_MAX) {
-        const uint64_t h = set_hash(op);
-        auto& bucket = set_index[h];
-        for (uint32_t cand : bucket)
-          if (same_set(*sets[cand], op)) { sid = cand; break; }
-        if (sid == UINT32_MAX) {
-          sid = static_cast<uint32_t>(sets.size());
-          sets.push_back(&op);
-          bucket.push_back(sid);
-        }
-        recent.emplace_back(&op, sid);
-        if (recent.size() > 16) recent.erase(recent.begin());
-      }
-      bt::Op o{};
-      o.kind = static_cast<uint8_t>(op.kind);
-      o.q = static_cast<uint8_t>(op.q);
-      o.q0 = static_cast<uint8_t>(op.qubits[0]);
-      o.q1 = static_cast<uint8_t>(op.q > 1 ? op.qubits[1] : 0);
-      o.set = sid;
-      o.channel = op.channel;
-      ops.push_back(o);
-      if (op.channel >= 0) ch_op.push_back(oi);
-      if (op.kind == QT_OP_GATE) B->gate_ops++;
-    }
-    for (const FusedGate& fg : f->gates) {
-      if (fg.targets.size() > static_cast<size_t>(bt::kMaxW))
-        return set_error(QT_ERR_UNSUPPORTED, "qt_batch_create: fused width %zu > %d in circuit %u", fg.targets.size(),
-                         bt::kMaxW, i);
-      bt::Gate g{};
-      g.w = static_cast<uint8_t>(fg.targets.size());
-      for (size_t b = 0; b < fg.targets.size(); ++b) g.t[b] = static_cast<uint8_t>(fg.targets[b]);
-      g.mat = static_cast<uint32_t>(fmat.size());
-      for (const cd& x : fg.def) fmat.push_back(make_float2(static_cast<float>(x.real()), static_cast<float>(x.imag())));
-      g.mem0 = static_cast<uint32_t>(members.size());
-      g.nmem = static_cast<uint32_t>(fg.members.size());
-      g.minpos = UINT32_MAX;
-      g.maxpos = 0;
-      for (uint32_t m : fg.members) {
-        members.push_back(m);
-        g.minpos = std::min(g.minpos, m);
-        g.maxpos = std::max(g.maxpos, m);
-      }
-      gates.push_back(g);
-      B->fused_gates++;
-    }
-    if (fmat.size() > 0x7fffffffu) return set_error(QT_ERR_UNSUPPORTED, "qt_batch_create: matrix table too large");
-  }
-  // operator-set tables
-  std::vector<bt::Set> dsets(sets.size());
-  for (size_t s = 0; s < sets.size(); ++s) {
-    const Op& op = *sets[s];
-    bt::Set& S = dsets[s];
-    S.nk = op.num_ops;
-    S.q = op.q;
-    S.def = static_cast<uint32_t>(op.def);
-    S.mat = static_cast<uint32_t>(fmat.size());
-    for (const cd& x : op.mats) fmat.push_back(make_float2(static_cast<float>(x.real()), static_cast<float>(x.imag())));
-    S.kraus = static_cast<uint32_t>(fmat.size());
-    const std::vector<cd>& kr = op.kind == QT_OP_GATE ? op.mats : op.kraus;
-    for (const cd& x : kr) fmat.push_back(make_float2(static_cast<float>(x.real()), static_cast<float>(x.imag())));
-    S.mtm = static_cast<uint32_t>(dmat.size());
-    for (const cd& x : op.mtm) { dmat.push_back(x.real()); dmat.push_back(x.imag()); }
-    S.pbar = static_cast<uint32_t>(dmat.size());
-    for (double p : op.pbar) dmat.push_back(p);
-    if (op.pbar.empty()) dmat.push_back(0.0);
-  }
-  // processing order: largest states first
-  B->order.resize(num);
-  for (uint32_t i = 0; i < num; ++i) B->order[i] = i;
-  std::stable_sort(B->order.begin(), B->order.end(),
-                   [&](uint32_t a, uint32_t b) { return B->traj[a].n > B->traj[b].n; });
-  for (uint32_t i = 0; i < num; ++i) {
-    B->traj[i].arena_off = B->total_amps;
-    B->total_amps += 1ull << B->traj[i].n;
-    if (B->traj[i].n > static_cast<uint32_t>(bt::kSmemNMax)) B->nglob++;
-  }
-  // ---- one device buffer for all tables ----
-  auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
-  size_t off = 0;
-  const size_t o_traj = off; off = align(off + sizeof(bt::Traj) * num);
-  const size_t o_ops = off; off = align(off + sizeof(bt::Op) * ops.size());
-  const size_t o_sets = off; off = align(off + sizeof(bt::Set) * dsets.size());
-  const size_t o_gates = off; off = align(off + sizeof(bt::Gate) * std::max<size_t>(gates.size(), 1));
-  const size_t o_mem = off; off = align(off + sizeof(uint32_t) * std::max<size_t>(members.size(), 1));
-  const size_t o_chop = off; off = align(off + sizeof(uint32_t) * std::max<size_t>(ch_op.size(), 1));
-  const size_t o_fmat = off; off = align(off + sizeof(float2) * fmat.size());
-  const size_t o_dmat = off; off = align(off + sizeof(double) * std::max<size_t>(dmat.size(), 1));
-  const size_t o_order = off; off = align(off + sizeof(uint32_t) * num);
-  if (!B->tables.alloc(off)) return set_error(QT_ERR_OUT_OF_MEMORY, "qt_batch_create: device tables (%zu bytes)", off);
-  std::vector<uint8_t> host(off, 0);
-  auto put = [&](size_t o, const void* src, size_t n) { if (n) std::memcpy(host.data() + o, src, n); };
-  put(o_traj, B->traj.data(), sizeof(bt::Traj) * num);
-  put(o_ops, ops.data(), sizeof(bt::Op) * ops.size());
-  put(o_sets, dsets.data(), sizeof(bt::Set) * dsets.size());
-  put(o_gates, gates.data(), sizeof(bt::Gate) * gates.size());
-  put(o_mem, members.data(), sizeof(uint32_t) * members.size());
-  put(o_chop, ch_op.data(), sizeof(uint32_t) * ch_op.size());
-  put(o_fmat, fmat.data(), sizeof(float2) * fmat.size());
-  put(o_dmat, dmat.data(), sizeof(double) * dmat.size());
-  put(o_order, B->order.data(), sizeof(uint32_t) * num);
-  cudaError_t e = cudaMemcpy(B->tables.p, host.data(), off, cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return set_error(QT_ERR_CUDA, "qt_batch_create: cudaMemcpy: %s", cudaGetErrorString(e));
-  uint8_t* base = static_cast<uint8_t*>(B->tables.p);
-  bt::Dev& d = B->dev;
-  d.traj = reinterpret_cast<const bt::Traj*>(base + o_traj);
-  d.ops = reinterpret_cast<const bt::Op*>(base + o_ops);
-  d.sets = reinterpret_cast<const bt::Set*>(base + o_sets);
-  d.gates = reinterpret_cast<const bt::Gate*>(base + o_gates);
-  d.members = reinterpret_cast<const uint32_t*>(base + o_mem);
-  d.ch_op = reinterpret_cast<const uint32_t*>(base + o_chop);
-  d.fmat = reinterpret_cast<const float2*>(base + o_fmat);
-  d.dmat = reinterpret_cast<const double*>(base + o_dmat);
-  d.order = reinterpret_cast<const uint32_t*>(base + o_order);
-  d.num = num;
-  // work counters of the two launches (2 x 4 B), error flag (4 B), run parameters at +16 (2 x 8 B)
-  if (!B->counter.alloc(32)) return set_error(QT_ERR_OUT_OF_MEMORY, "qt_batch_create: counter");
-  d.counter = static_cast<unsigned int*>(B->counter.p);
-  d.err = reinterpret_cast<int*>(static_cast<unsigned int*>(B->counter.p) + 2);
-  d.run = reinterpret_cast<const uint64_t*>(static_cast<uint8_t*>(B->counter.p) + 16);
-  if (cudaMallocHost(&B->hrun, 2 * sizeof(uint64_t)) != cudaSuccess)
-    return set_error(QT_ERR_OUT_OF_MEMORY, "qt_batch_create: pinned parameters");
-  if (cudaStreamCreateWithFlags(&B->side, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&B->ev_join, cudaEventDisableTiming) != cudaSuccess)
-    return set_error(QT_ERR_CUDA, "qt_batch_create: side stream");
+  qt_status s = pack_batch(B.get(), num, fused, nullptr, "qt_batch_create", nullptr);
+  if (s == QT_OK) s = init_batch_runtime(B.get(), "qt_batch_create");
+  if (s != QT_OK) return s;
+  const cudaError_t e = cudaStreamSynchronize(nullptr);   // the tables are on the device
+  if (e != cudaSuccess) return set_error(QT_ERR_CUDA, "qt_batch_create: %s", cudaGetErrorString(e));
   *out = B.release();
   return QT_OK;
 }
@@ -1059,28 +1156,8 @@ qt_status qt_batch_run(qt_batch* b, const qt_batch_params* p) {
   }
   b->hrun[0] = p->seed;
   b->hrun[1] = p->first_traj;
-  // the matrix area (64 x 64 complex64) and, for global states, its 16 x 16
-  // (x, x, y, y) expansion behind it
-  const size_t smem_mat = sizeof(float2) * (1u << (2 * bt::kMaxW)) + sizeof(float4) * 256;
-  const size_t smem = (sizeof(float2) << bt::kSmemNMax) + smem_mat;
-  static PerDevice attr_set;
-  const cudaError_t attr = static_cast<cudaError_t>(attr_set.get([&] {
-    cudaError_t e1 = cudaFuncSetAttribute(bt::k_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          static_cast<int>(smem));
-    if (e1 == cudaSuccess)
-      e1 = cudaFuncSetAttribute(bt::k_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                static_cast<int>(smem_mat));
-    return static_cast<int>(e1);
-  }));
+  const cudaError_t attr = batch_kernel_attrs();
   if (attr != cudaSuccess) return set_error(QT_ERR_CUDA, "qt_batch_run: smem attribute: %s", cudaGetErrorString(attr));
-  const uint32_t nglob = b->nglob, nsh = b->num - b->nglob;
-  const unsigned grid_g = static_cast<unsigned>(std::min<uint64_t>(sm_count(), nglob));
-  const unsigned grid_s = static_cast<unsigned>(std::min<uint64_t>(sm_count(), nsh));
-  bt::Dev dg = d, ds = d;
-  dg.num = nglob;
-  ds.order = d.order + nglob;
-  ds.num = nsh;
-  ds.counter = d.counter + 1;
   struct Events {                   // the run's timing events, destroyed on every return
     cudaEvent_t a = nullptr, b = nullptr;
     ~Events() {
@@ -1096,22 +1173,7 @@ qt_status qt_batch_run(qt_batch* b, const qt_batch_params* p) {
     cudaError_t r = cudaMemcpyAsync(static_cast<uint8_t*>(b->counter.p) + 16, b->hrun, 2 * sizeof(uint64_t),
                                     cudaMemcpyHostToDevice, s);
     if (r != cudaSuccess) return r;
-    r = cudaMemsetAsync(b->counter.p, 0, 2 * sizeof(unsigned int) + sizeof(int), s);
-    if (r != cudaSuccess) return r;
-    const bool both = nglob && nsh;
-    if (both) {
-      r = cudaEventRecord(b->ev_fork, s);
-      if (r == cudaSuccess) r = cudaStreamWaitEvent(b->side, b->ev_fork, 0);
-      if (r != cudaSuccess) return r;
-    }
-    if (nglob) bt::k_batch<true><<<grid_g, threads_glob, smem_mat, s>>>(dg);
-    if (nsh) bt::k_batch<false><<<grid_s, threads, smem, both ? b->side : s>>>(ds);
-    r = cudaGetLastError();
-    if (r == cudaSuccess && both) {
-      r = cudaEventRecord(b->ev_join, b->side);
-      if (r == cudaSuccess) r = cudaStreamWaitEvent(s, b->ev_join, 0);
-    }
-    return r;
+    return launch_classes(b, d, threads, threads_glob, s);
   };
   e = cudaEventRecord(e0, st);
   if (e == cudaSuccess && p->use_graph && st) {
@@ -1279,3 +1341,83 @@ qt_status qt_batch_autotune(uint32_t num, const qt_circuit* const* circuits, uin
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// merged launches of the serving form (the batch lane)
+// ---------------------------------------------------------------------------
+namespace qt {
+
+struct BatchLane {
+  qt_batch B;
+  cudaStream_t st = nullptr;
+  uint32_t max_n = 0;
+  uint64_t slot = 0;                // amplitudes per global-memory state slot
+  std::vector<const qt_fused*> fused;
+};
+
+qt_status lane_create(uint32_t max_n, void* stream, BatchLane** out) {
+  if (!out) return set_error(QT_ERR_INVALID_ARG, "lane_create: NULL argument");
+  *out = nullptr;
+  if (max_n < 1 || max_n > static_cast<uint32_t>(bt::kMaxN))
+    return set_error(QT_ERR_INVALID_ARG, "lane_create: max_n %u outside 1..%d", max_n, bt::kMaxN);
+  std::unique_ptr<BatchLane> L(new (std::nothrow) BatchLane());
+  if (!L) return set_error(QT_ERR_OUT_OF_MEMORY, "lane_create: host allocation");
+  L->st = static_cast<cudaStream_t>(stream);
+  L->max_n = max_n;
+  qt_status s = init_batch_runtime(&L->B, "lane_create");
+  if (s != QT_OK) return s;
+  if (max_n > static_cast<uint32_t>(bt::kSmemNMax)) {
+    L->slot = 1ull << max_n;
+    if (!L->B.arena.alloc(sizeof(float2) * L->slot * sm_count()))
+      return set_error(QT_ERR_OUT_OF_MEMORY, "lane_create: state slots (%u qubits)", max_n);
+  }
+  *out = L.release();
+  return QT_OK;
+}
+
+void lane_destroy(BatchLane* l) { delete l; }
+
+qt_status lane_run(BatchLane* L, uint32_t num, const LaneTraj* tr, uint64_t* samples, uint32_t* flushes) {
+  if (!L || !tr || num == 0) return set_error(QT_ERR_INVALID_ARG, "lane_run: NULL argument or no trajectories");
+  qt_batch* b = &L->B;
+  L->fused.resize(num);
+  for (uint32_t i = 0; i < num; ++i) {
+    if (!tr[i].f) return set_error(QT_ERR_INVALID_ARG, "lane_run: trajectory %u has no circuit", i);
+    if (tr[i].f->c->n > L->max_n)
+      return set_error(QT_ERR_UNSUPPORTED, "lane_run: %u qubits > the lane's %u", tr[i].f->c->n, L->max_n);
+    L->fused[i] = tr[i].f;
+  }
+  qt_status s = pack_batch(b, num, L->fused.data(), tr, "lane_run", L->st);
+  if (s != QT_OK) return s;
+  auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
+  size_t off = 0;
+  const size_t o_kraus = off; off = align(off + sizeof(int32_t) * std::max<uint32_t>(b->total_ch, 1));
+  const size_t o_stage = off; off = align(off + sizeof(int32_t) * std::max<uint32_t>(b->total_ch, 1));
+  const size_t o_samp = off; off = align(off + sizeof(uint64_t) * std::max<uint64_t>(b->lane_samples, 1));
+  const size_t o_flush = off; off = align(off + sizeof(uint32_t) * num);
+  const size_t o_gflag = off; off = align(off + std::max<uint64_t>(b->total_gates, 1));
+  if (b->outs.bytes < off && !b->outs.alloc(off)) return set_error(QT_ERR_OUT_OF_MEMORY, "lane_run: outputs");
+  uint8_t* o = static_cast<uint8_t*>(b->outs.p);
+  bt::Dev d = b->dev;
+  d.kraus = reinterpret_cast<int32_t*>(o + o_kraus);
+  d.stage = reinterpret_cast<int32_t*>(o + o_stage);
+  d.samples = reinterpret_cast<uint64_t*>(o + o_samp);
+  d.flushes = reinterpret_cast<uint32_t*>(o + o_flush);
+  d.gflag = o + o_gflag;
+  d.arena = static_cast<float2*>(b->arena.p);
+  d.slot_amps = L->slot;
+  d.keep = 0;
+  d.S = 0;
+  d.per_traj = 1;
+  cudaError_t e = batch_kernel_attrs();
+  if (e == cudaSuccess) e = launch_classes(b, d, 512, 512, L->st);
+  if (e == cudaSuccess && b->lane_samples)
+    e = cudaMemcpyAsync(samples, d.samples, sizeof(uint64_t) * b->lane_samples, cudaMemcpyDeviceToHost, L->st);
+  if (e == cudaSuccess && flushes)
+    e = cudaMemcpyAsync(flushes, d.flushes, sizeof(uint32_t) * num, cudaMemcpyDeviceToHost, L->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(L->st);
+  if (e != cudaSuccess) return set_error(QT_ERR_CUDA, "lane_run: %s", cudaGetErrorString(e));
+  return QT_OK;
+}
+
+}  // namespace qt

@@ -80,3 +80,28 @@ qt_status fuse_circuit(const Circuit& c, uint32_t kmax, Fused& f);
 
 struct qt_circuit : qt::Circuit {};
 struct qt_fused : qt::Fused {};
+
+namespace qt {
+
+// ---- merged batched launches (batch.cu), the serving form's batch lane -----
+// One trajectory of a merged launch: its fused circuit, Philox key,
+// trajectory id and sample count.  Trajectories of different requests share
+// one persistent launch; each one's results depend only on these fields.
+struct LaneTraj {
+  const qt_fused* f;
+  uint64_t seed, traj;
+  uint32_t S;
+};
+struct BatchLane;
+// A lane owns its stream-ordered device buffers (tables and outputs grow as
+// needed; the global-memory state slots are sized once for states of up to
+// max_n qubits) and reuses them across launches.
+qt_status lane_create(uint32_t max_n, void* stream, BatchLane** out);
+void lane_destroy(BatchLane* l);
+// Run every trajectory (n <= max_n) in one launch of each state class on the
+// lane's stream; samples: sum of S entries in trajectory order; flushes: one
+// count per trajectory.  Blocks until the results are on the host.
+qt_status lane_run(BatchLane* l, uint32_t num, const LaneTraj* tr, uint64_t* samples, uint32_t* flushes);
+
+
+}  // namespace qt

@@ -1,23 +1,41 @@
 // Serving form: a request loop with continuous batching on one GPU.
 //
 // Trajectory requests (a fused circuit, a seed, a trajectory range, a sample
-// count) are submitted as they arrive.  A fixed set of workers, each with
-// its own CUDA stream, takes requests in arrival order as soon as a worker is
-// free and the request's device footprint fits the memory budget
-// (8 * 2^n bytes per resident state, the paper's memory rule of Sec. IV.A),
-// so requests that arrive while others run are admitted as slots and memory
-// free up and their kernels overlap on the device.  Small states run their
-// trajectories in one batched persistent launch (batch.cu), larger ones the
-// plain trajectory loop (runtime.cu); either way every request's results
-// depend only on its own circuit, seed and trajectory ids, so a request gives
-// the same result alone and in any mix.
+// count) are submitted as they arrive and served by two kinds of executor:
+//
+//   - the batch lane: requests of small states (n <= 14, or up to
+//     small_n_max with >= 64 trajectories) wait in their own queue; whenever
+//     the lane is free it takes every queued small request at once and runs
+//     all their trajectories -- each with its own circuit, seed and
+//     trajectory id -- in one merged launch of the batched persistent kernel
+//     (batch.cu), whose CTAs take trajectories from a device work counter.
+//     Requests that arrive during a launch join the next one.  The lane's
+//     device buffers are kept between launches; the global-memory state
+//     slots it needs for states above 2^14 amplitudes are reserved against
+//     the budget once, when the server starts;
+//   - plain workers: the other requests run the plain trajectory loop
+//     (runtime.cu), each worker on its own CUDA stream, admitted in arrival
+//     order as soon as a worker is free and the request's device footprint
+//     fits the memory budget (8 * 2^n bytes per resident state, the memory
+//     rule of Sec. IV.A).  The trajectories of one request share their
+//     default-choice prefix (QT_FLAG_SHARE_PREFIX): one state advances along
+//     the operators every trajectory applies, and each trajectory copies it
+//     at its first non-default channel, so a request holds two states.
+//
+// Requests that arrive while others run are admitted as the lane and slots
+// and memory free up, and their kernels overlap on the device.  Every
+// request's results depend only on its own circuit, seed and trajectory ids
+// (the batched kernel runs each trajectory in one CTA with a fixed reduction
+// order; the plain loop's prefix sharing is decided by the request alone), so
+// a request gives the same result alone and in any mix.
 //
 // Failure handling is host-side: a request that hits an out-of-memory error
-// is deferred and retried, a request whose worker thread died is requeued by
-// the watchdog and a replacement worker is started, and queued requests can
-// be cancelled.  qt_server_inject drives these paths deterministically (for
-// tests); a dry-run mode replaces the GPU work by a timed wait so the
-// scheduling logic runs without a GPU.
+// is deferred and retried, a request whose executor thread died is requeued
+// by the watchdog (every request of a merged launch, for the lane) and a
+// replacement thread is started, and queued requests can be cancelled.
+// qt_server_inject drives these paths deterministically (for tests); a
+// dry-run mode replaces the GPU work by a timed wait so the scheduling logic
+// runs without a GPU.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -47,6 +65,10 @@ double now_s() {
 
 enum ReqState : int32_t { kQueued = 0, kRunning = 1, kDone = 2, kFailed = 3, kCancelled = 4 };
 
+constexpr uint32_t kSmemStateMaxN = 14;       // states the batched kernel holds in shared memory
+constexpr uint64_t kLaneMaxTraj = 1u << 15;   // trajectories per merged launch
+constexpr uint64_t kScratch = 16ull << 20;    // per-request scratch allowance
+
 struct Req {
   const qt_fused* f = nullptr;
   qt_server_request r{};
@@ -68,7 +90,7 @@ struct Worker {
   cudaStream_t stream = nullptr;
   std::atomic<bool> finished{false};
   std::atomic<bool> crashed{false};
-  uint64_t current = 0;          // request being run (0: none)
+  std::vector<uint64_t> held;    // requests being run (one, or a merged launch for the lane)
 };
 
 }  // namespace
@@ -79,47 +101,53 @@ using namespace qt;
 struct qt_server {
   qt_server_config cfg{};
   int device = 0;
-  uint32_t sms = 152;        // SMs of the device (sizes the batched form's arena)
+  uint32_t sms = 152;        // SMs of the device (sizes the lane's state slots)
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
-  std::deque<uint64_t> queue;
+  std::deque<uint64_t> queue;     // plain-loop requests
+  std::deque<uint64_t> bqueue;    // requests for the batch lane
   std::unordered_map<uint64_t, Req> reqs;
   uint64_t next_id = 1;
   uint64_t inflight = 0, peak_inflight = 0;
   uint32_t requeued = 0, deferred = 0;
+  uint64_t lane_launches = 0, lane_trajectories = 0;
   bool stop = false;
-  std::vector<std::unique_ptr<Worker>> workers;
+  std::vector<std::unique_ptr<Worker>> workers;   // plain workers, then the lane (if any)
+  uint32_t lane_max_n = 0;                        // 0: no lane
+  uint64_t lane_bytes = 0;                        // reserved for the lane's state slots
+  BatchLane* lane = nullptr;
   std::thread watchdog;
   // fault injection (host side)
   uint32_t inj_exit = 0, inj_oom = 0;
 
+  bool is_lane(size_t w) const { return lane_max_n && w + 1 == workers.size(); }
   void start_worker(size_t w);
   void worker_loop(size_t w);
+  void lane_loop(size_t w);
   void watchdog_loop();
   qt_status execute(Req& q, cudaStream_t st);
+  qt_status execute_lane(const std::vector<uint64_t>& ids);
+  void finish(uint64_t id, qt_status s, const std::string& msg);
 };
 
 namespace qt {
 namespace {
 
-uint64_t footprint(uint32_t n, bool batched, uint32_t sms) {
+// Device memory a plain-loop request holds while it runs: its states (two
+// with the shared prefix, which needs more than one trajectory) and scratch.
+uint64_t footprint(uint32_t n, uint32_t num_traj, bool share) {
   const uint64_t state = 8ull << n;
-  // batched form: states <= 2^14 sit in shared memory; larger ones take one
-  // global slot per SM (the arena qt_batch_run sizes by the SM count).  Plain
-  // loop: one resident state.  Plus scratch.
-  uint64_t b = batched ? (n > 14 ? state * sms : 0) : state;
-  b += (16ull << 20) + (state >> 8);
-  return b;
+  return state * (share && num_traj > 1 ? 2 : 1) + kScratch + (state >> 8);
 }
 
-// One trajectory per SM in the batched kernel: worth it for states that fit
-// in shared memory, and for larger ones (up to small_n_max) only when the
-// request has enough trajectories to occupy the GPU.
-bool use_batched(const qt_server_config& c, const qt_fused* f, uint32_t num_traj) {
-  if (c.small_n_max == 0 || f->c->n > c.small_n_max || f->c->n > 20) return false;
-  if (f->c->n > 14 && num_traj < 64) return false;
+// One trajectory per CTA in the batched kernel: worth it for states that fit
+// in shared memory, and for larger ones (up to the lane's limit) only when
+// the request has enough trajectories to occupy the GPU.
+bool use_batched(uint32_t lane_max_n, const qt_fused* f, uint32_t num_traj) {
+  if (lane_max_n == 0 || f->c->n > lane_max_n) return false;
+  if (f->c->n > kSmemStateMaxN && num_traj < 64) return false;
   for (const auto& g : f->gates)
-    if (g.targets.size() > 4) return false;
+    if (g.targets.size() > 6) return false;
   for (const auto& op : f->c->ops)
     if (op.q > 2) return false;
   return true;
@@ -136,26 +164,6 @@ qt_status qt_server::execute(Req& q, cudaStream_t st) {
     q.samples.assign(static_cast<size_t>(q.r.num_traj) * q.r.samples_per_traj, 0);
     return QT_OK;
   }
-  if (q.batched) {
-    std::vector<const qt_fused*> fs(q.r.num_traj, q.f);
-    qt_batch* b = nullptr;
-    qt_status s = qt_batch_create(q.r.num_traj, fs.data(), &b);
-    if (s != QT_OK) return s;
-    qt_batch_params p{};
-    p.seed = q.r.seed;
-    p.first_traj = q.r.first_traj;
-    p.samples_per_traj = q.r.samples_per_traj;
-    p.stream = st;
-    s = qt_batch_run(b, &p);
-    if (s == QT_OK) {
-      q.samples.assign(static_cast<size_t>(q.r.num_traj) * q.r.samples_per_traj, 0);
-      s = qt_batch_samples(b, q.samples.data(), q.samples.size());
-      qt_batch_stats_t bs{};
-      if (s == QT_OK && qt_batch_stats(b, &bs) == QT_OK) q.flushes = bs.flushes;
-    }
-    qt_batch_destroy(b);
-    return s;
-  }
   qt_run_params p{};
   p.seed = q.r.seed;
   p.first_traj = q.r.first_traj;
@@ -163,6 +171,7 @@ qt_status qt_server::execute(Req& q, cudaStream_t st) {
   p.mode = QT_DELAYED;
   p.precision = QT_FP32;
   p.samples_per_traj = q.r.samples_per_traj;
+  p.flags = (cfg.flags & QT_SERVER_NO_SHARED_PREFIX) ? 0u : QT_FLAG_SHARE_PREFIX;
   p.stream = st;
   qt_run* run = nullptr;
   qt_status s = qt_run_trajectories(q.f, &p, &run);
@@ -175,13 +184,70 @@ qt_status qt_server::execute(Req& q, cudaStream_t st) {
   return s;
 }
 
+// One merged launch over every trajectory of the requests `ids`.
+qt_status qt_server::execute_lane(const std::vector<uint64_t>& ids) {
+  std::vector<LaneTraj> tr;
+  std::vector<Req*> rq;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    for (uint64_t id : ids) rq.push_back(&reqs[id]);
+  }
+  uint64_t nsamp = 0;
+  for (Req* q : rq)
+    for (uint32_t t = 0; t < q->r.num_traj; ++t) {
+      tr.push_back(LaneTraj{q->f, q->r.seed, q->r.first_traj + t, q->r.samples_per_traj});
+      nsamp += q->r.samples_per_traj;
+    }
+  std::vector<uint64_t> samples(nsamp, 0);
+  std::vector<uint32_t> flushes(tr.size(), 0);
+  if (cfg.flags & QT_SERVER_DRY_RUN) {
+    double us = 20.0;
+    for (Req* q : rq) us += 1e-4 * static_cast<double>(q->r.num_traj) * static_cast<double>(1ull << q->n);
+    std::this_thread::sleep_for(std::chrono::microseconds(static_cast<int64_t>(std::min(us, 2e5))));
+  } else {
+    const qt_status s = lane_run(lane, static_cast<uint32_t>(tr.size()), tr.data(), samples.data(), flushes.data());
+    if (s != QT_OK) return s;
+  }
+  uint64_t so = 0, to = 0;
+  for (Req* q : rq) {
+    const size_t ns = static_cast<size_t>(q->r.num_traj) * q->r.samples_per_traj;
+    q->samples.assign(samples.begin() + so, samples.begin() + so + ns);
+    q->flushes = 0;
+    for (uint32_t t = 0; t < q->r.num_traj; ++t) q->flushes += flushes[to + t];
+    so += ns;
+    to += q->r.num_traj;
+  }
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    lane_launches++;
+    lane_trajectories += tr.size();
+  }
+  return QT_OK;
+}
+
+// Record the outcome of a run (caller holds mu): an allocation failure puts
+// the request back at the head of its queue (up to 4 attempts).
+void qt_server::finish(uint64_t id, qt_status s, const std::string& msg) {
+  Req& q = reqs[id];
+  if (s == QT_ERR_OUT_OF_MEMORY && q.attempts < 4 && q.state != kCancelled) {
+    q.state = kQueued;                 // deferred, not lost: back to the head of the queue
+    (q.batched ? bqueue : queue).push_front(id);
+    deferred++;
+  } else {
+    q.state = s == QT_OK ? kDone : kFailed;
+    q.status = s;
+    q.err = msg;
+    q.t_done = now_s();
+  }
+}
+
 void qt_server::worker_loop(size_t w) {
   Worker& me = *workers[w];
   struct Done {
     Worker& w;
     ~Done() { w.finished = true; }
   } done{me};
-  cudaSetDevice(device);
+  if (!(cfg.flags & QT_SERVER_DRY_RUN)) cudaSetDevice(device);
   for (;;) {
     uint64_t id = 0;
     Req* q = nullptr;
@@ -203,7 +269,7 @@ void qt_server::worker_loop(size_t w) {
       if (q->attempts == 1) q->t_start = now_s();
       inflight += q->bytes;
       peak_inflight = std::max(peak_inflight, inflight);
-      me.current = id;
+      me.held.assign(1, id);
       if (inj_exit) {                 // injected fault: this worker dies holding the request
         --inj_exit;
         me.crashed = true;
@@ -225,17 +291,64 @@ void qt_server::worker_loop(size_t w) {
     {
       std::lock_guard<std::mutex> lk(mu);
       inflight -= q->bytes;
-      me.current = 0;
-      if (s == QT_ERR_OUT_OF_MEMORY && q->attempts < 4 && q->state != kCancelled) {
-        q->state = kQueued;                 // deferred, not lost: back to the head of the queue
-        queue.push_front(id);
-        deferred++;
-      } else {
-        q->state = s == QT_OK ? kDone : kFailed;
-        q->status = s;
-        q->err = msg;
-        q->t_done = now_s();
+      me.held.clear();
+      finish(id, s, msg);
+    }
+    cv_work.notify_all();
+    cv_done.notify_all();
+  }
+}
+
+void qt_server::lane_loop(size_t w) {
+  Worker& me = *workers[w];
+  struct Done {
+    Worker& w;
+    ~Done() { w.finished = true; }
+  } done{me};
+  if (!(cfg.flags & QT_SERVER_DRY_RUN)) cudaSetDevice(device);
+  for (;;) {
+    std::vector<uint64_t> ids;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      cv_work.wait(lk, [&] { return stop || !bqueue.empty(); });
+      if (stop) return;
+      // every queued small request, in arrival order, up to the launch's cap
+      uint64_t traj = 0;
+      while (!bqueue.empty()) {
+        Req& q = reqs[bqueue.front()];
+        if (!ids.empty() && traj + q.r.num_traj > kLaneMaxTraj) break;
+        traj += q.r.num_traj;
+        ids.push_back(bqueue.front());
+        bqueue.pop_front();
+        q.state = kRunning;
+        q.worker = static_cast<int32_t>(w);
+        q.attempts++;
+        if (q.attempts == 1) q.t_start = now_s();
       }
+      me.held = ids;
+      if (inj_exit) {                 // injected fault: the lane dies holding its launch
+        --inj_exit;
+        me.crashed = true;
+        return;
+      }
+    }
+    qt_status s;
+    bool oom = false;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      if (inj_oom) { --inj_oom; oom = true; }
+    }
+    if (oom) {
+      s = set_error(QT_ERR_OUT_OF_MEMORY, "injected allocation failure");
+    } else {
+      s = execute_lane(ids);
+    }
+    std::string msg = s == QT_OK ? std::string() : std::string(qt_last_error());
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      me.held.clear();
+      // deferred requests go back to the head of the queue in their order
+      for (auto it = ids.rbegin(); it != ids.rend(); ++it) finish(*it, s, msg);
     }
     cv_work.notify_all();
     cv_done.notify_all();
@@ -245,7 +358,8 @@ void qt_server::worker_loop(size_t w) {
 void qt_server::start_worker(size_t w) {
   workers[w]->finished = false;
   workers[w]->crashed = false;
-  workers[w]->th = std::thread([this, w] { worker_loop(w); });
+  if (is_lane(w)) workers[w]->th = std::thread([this, w] { lane_loop(w); });
+  else workers[w]->th = std::thread([this, w] { worker_loop(w); });
 }
 
 void qt_server::watchdog_loop() {
@@ -256,18 +370,18 @@ void qt_server::watchdog_loop() {
     for (size_t w = 0; w < workers.size(); ++w) {
       Worker& k = *workers[w];
       if (!k.finished || !k.crashed) continue;
-      // the worker died holding a request: requeue it by id, start a replacement
-      const uint64_t id = k.current;
-      if (id) {
-        Req& q = reqs[id];
-        inflight -= q.bytes;
+      // the thread died holding requests: requeue them by id (in their
+      // order, at the head of their queue) and start a replacement
+      for (auto it = k.held.rbegin(); it != k.held.rend(); ++it) {
+        Req& q = reqs[*it];
+        if (!q.batched) inflight -= q.bytes;
         if (q.state == kRunning) {
           q.state = kQueued;
-          queue.push_front(id);
+          (q.batched ? bqueue : queue).push_front(*it);
           requeued++;
         }
-        k.current = 0;
       }
+      k.held.clear();
       lk.unlock();
       if (k.th.joinable()) k.th.join();
       lk.lock();
@@ -289,19 +403,40 @@ qt_status qt_server_create(const qt_server_config* cfg, qt_server** out) {
   std::unique_ptr<qt_server> S(new (std::nothrow) qt_server());
   if (!S) return set_error(QT_ERR_OUT_OF_MEMORY, "qt_server_create: host allocation");
   S->cfg = *cfg;
-  if (!(cfg->flags & QT_SERVER_DRY_RUN)) {
+  const bool dry = (cfg->flags & QT_SERVER_DRY_RUN) != 0;
+  if (!dry) {
     if (cudaGetDevice(&S->device) != cudaSuccess) return set_error(QT_ERR_CUDA, "qt_server_create: no CUDA device");
     S->sms = static_cast<uint32_t>(sm_count());
   }
-  S->workers.resize(cfg->max_slots);
-  for (uint32_t w = 0; w < cfg->max_slots; ++w) {
+  // the batch lane: states up to small_n_max (<= 20); the slots of states
+  // above 2^14 amplitudes (one per SM) are reserved against the budget, and
+  // the lane keeps to shared-memory states when they would take more than
+  // half of it
+  if (cfg->small_n_max > 0) {
+    S->lane_max_n = std::min<uint32_t>(std::max<uint32_t>(cfg->small_n_max, kSmemStateMaxN), 20);
+    if (S->lane_max_n > kSmemStateMaxN) {
+      S->lane_bytes = (8ull << S->lane_max_n) * S->sms;
+      if (S->lane_bytes > cfg->budget_bytes / 2) {
+        S->lane_max_n = kSmemStateMaxN;
+        S->lane_bytes = 0;
+      }
+    }
+    S->inflight = S->peak_inflight = S->lane_bytes;
+  }
+  const uint32_t nw = cfg->max_slots + (S->lane_max_n ? 1 : 0);
+  S->workers.resize(nw);
+  for (uint32_t w = 0; w < nw; ++w) {
     S->workers[w] = std::make_unique<Worker>();
-    if (!(cfg->flags & QT_SERVER_DRY_RUN)) {
+    if (!dry) {
       if (cudaStreamCreateWithFlags(&S->workers[w]->stream, cudaStreamNonBlocking) != cudaSuccess)
         return set_error(QT_ERR_CUDA, "qt_server_create: cudaStreamCreate");
     }
   }
-  for (uint32_t w = 0; w < cfg->max_slots; ++w) S->start_worker(w);
+  if (S->lane_max_n && !dry) {
+    const qt_status s = lane_create(S->lane_max_n, S->workers[nw - 1]->stream, &S->lane);
+    if (s != QT_OK) return s;
+  }
+  for (uint32_t w = 0; w < nw; ++w) S->start_worker(w);
   S->watchdog = std::thread([s = S.get()] { s->watchdog_loop(); });
   *out = S.release();
   return QT_OK;
@@ -315,17 +450,19 @@ qt_status qt_server_submit(qt_server* s, const qt_fused* f, const qt_server_requ
   q.f = f;
   q.r = *r;
   q.n = f->c->n;
-  q.batched = use_batched(s->cfg, f, r->num_traj);
-  q.bytes = footprint(q.n, q.batched, s->sms);
-  if (q.bytes > s->cfg.budget_bytes)
+  q.batched = use_batched(s->lane_max_n, f, r->num_traj) && r->num_traj <= kLaneMaxTraj;
+  q.bytes = q.batched ? 0 : footprint(q.n, r->num_traj, !(s->cfg.flags & QT_SERVER_NO_SHARED_PREFIX));
+  // (the lane's memory is reserved up front)
+  if (q.bytes + s->lane_bytes > s->cfg.budget_bytes)
     return set_error(QT_ERR_OUT_OF_MEMORY, "qt_server_submit: footprint %llu bytes exceeds the budget %llu",
                      static_cast<unsigned long long>(q.bytes), static_cast<unsigned long long>(s->cfg.budget_bytes));
   q.t_submit = now_s();
   {
     std::lock_guard<std::mutex> lk(s->mu);
     const uint64_t i = s->next_id++;
+    const bool b = q.batched;
     s->reqs.emplace(i, std::move(q));
-    s->queue.push_back(i);
+    (b ? s->bqueue : s->queue).push_back(i);
     *id = i;
   }
   s->cv_work.notify_all();
@@ -366,7 +503,8 @@ qt_status qt_server_cancel(qt_server* s, uint64_t id) {
   if (it == s->reqs.end()) return set_error(QT_ERR_INVALID_ARG, "qt_server_cancel: unknown request");
   if (it->second.state != kQueued)
     return set_error(QT_ERR_INVALID_ARG, "qt_server_cancel: request %llu is not queued", (unsigned long long)id);
-  s->queue.erase(std::remove(s->queue.begin(), s->queue.end(), id), s->queue.end());
+  std::deque<uint64_t>& qu = it->second.batched ? s->bqueue : s->queue;
+  qu.erase(std::remove(qu.begin(), qu.end(), id), qu.end());
   it->second.state = kCancelled;
   it->second.t_done = now_s();
   s->cv_done.notify_all();
@@ -424,6 +562,9 @@ qt_status qt_server_stats(qt_server* s, qt_server_stats_t* out) {
   out->peak_inflight_bytes = s->peak_inflight;
   out->requeued = s->requeued;
   out->deferred = s->deferred;
+  out->lane_bytes = s->lane_bytes;
+  out->lane_launches = s->lane_launches;
+  out->lane_trajectories = s->lane_trajectories;
   for (const auto& kv : s->reqs) {
     if (kv.second.state == kQueued) out->queued++;
     else if (kv.second.state == kRunning) out->running++;
@@ -455,6 +596,7 @@ void qt_server_destroy(qt_server* s) {
   if (s->watchdog.joinable()) s->watchdog.join();
   for (auto& w : s->workers)
     if (w->th.joinable()) w->th.join();
+  if (s->lane) lane_destroy(s->lane);
   for (auto& w : s->workers)
     if (w->stream) cudaStreamDestroy(w->stream);
   delete s;

@@ -101,10 +101,12 @@ class qt_server_stats_t(C.Structure):
     _fields_ = [("budget", C.c_uint64), ("inflight_bytes", C.c_uint64), ("peak_inflight_bytes", C.c_uint64),
                 ("queued", C.c_uint32), ("running", C.c_uint32), ("done", C.c_uint32), ("failed", C.c_uint32),
                 ("workers_alive", C.c_uint32), ("requeued", C.c_uint32), ("deferred", C.c_uint32),
-                ("pad", C.c_uint32)]
+                ("pad", C.c_uint32), ("lane_bytes", C.c_uint64), ("lane_launches", C.c_uint64),
+                ("lane_trajectories", C.c_uint64)]
 
 
 QT_SERVER_DRY_RUN = 1
+QT_SERVER_NO_SHARED_PREFIX = 2
 QT_FAULT_WORKER_EXIT, QT_FAULT_ALLOC = 1, 2
 
 
@@ -614,11 +616,15 @@ def fuse_by_class(circuits, tuning, threads=0):
 # serving form
 # ----------------------------------------------------------------------------
 class Server:
-    """qt_server: continuous-batching request loop (one stream per slot)."""
+    """qt_server: continuous-batching request loop (plain-loop workers, one stream
+    per slot, and a batch lane that merges small requests into shared launches)."""
 
-    def __init__(self, budget_bytes, max_slots=8, small_n_max=16, dry_run=False):
+    def __init__(self, budget_bytes, max_slots=8, small_n_max=16, dry_run=False, share_prefix=True):
+        """small_n_max: the batch lane's limit (0: no lane); share_prefix=False: plain
+        workers run each trajectory on its own (QT_SERVER_NO_SHARED_PREFIX)."""
         cfg = qt_server_config(int(budget_bytes), int(max_slots), int(small_n_max),
-                               QT_SERVER_DRY_RUN if dry_run else 0)
+                               (QT_SERVER_DRY_RUN if dry_run else 0) |
+                               (0 if share_prefix else QT_SERVER_NO_SHARED_PREFIX))
         self.h = C.c_void_p()
         _check(load().qt_server_create(C.byref(cfg), C.byref(self.h)))
         self._fused = {}

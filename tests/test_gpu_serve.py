@@ -44,6 +44,8 @@ def test_alone_equals_in_mix(qt):
     mixed = [mix.result(i)[0] for i in ids]
     st = mix.stats()
     assert st["done"] == len(reqs) and st["peak_inflight_bytes"] <= budget
+    nb = sum(mix.info(i)["batched"] for i in ids)
+    assert nb >= 2 and 1 <= st["lane_launches"] < nb           # small requests shared launches
     mix.close()
     alone_srv = qt.Server(budget, max_slots=1, small_n_max=16)
     for (r, f), m in zip(reqs, mixed):
@@ -70,6 +72,61 @@ def test_served_requests_match_oracle(qt, orc):
             if np.any(ref["margin"] <= MARGIN):
                 continue
             want, margin = orc.sample(ref["state"], r["seed"], t, r["samples"])
+            ok = margin > MARGIN
+            np.testing.assert_array_equal(smp[t][ok], want[ok])
+    srv.close()
+
+
+def test_served_plain_requests_match_oracle(qt, orc):
+    """Requests on the plain workers (their trajectories share the default-choice
+    prefix) against the oracle, and against the server's per-trajectory loop."""
+    reqs = [x for x in _requests(qt, count=16, seed=11) if 15 <= x[0]["n"] <= 18][:2]
+    assert reqs
+    shared = qt.Server(16 << 30, max_slots=2, small_n_max=0)
+    plain = qt.Server(16 << 30, max_slots=2, small_n_max=0, share_prefix=False)
+    for r, f in reqs:
+        T = min(r["num_traj"], 6)
+        out = []
+        for srv in (shared, plain):
+            i = srv.submit(f, seed=r["seed"], first_traj=0, num_traj=T, samples_per_traj=r["samples"])
+            srv.wait(i, timeout_s=300)
+            smp, inf = srv.result(i)
+            assert inf["batched"] == 0
+            out.append(smp)
+        circ = qs.request_compact(r).to_circuit()
+        for t in range(T):
+            ref = orc.run_trajectory(circ, orc.DELAYED, seed=r["seed"], traj=t)
+            if np.any(ref["margin"] <= MARGIN):
+                continue
+            want, margin = orc.sample(ref["state"], r["seed"], t, r["samples"])
+            ok = margin > MARGIN
+            for smp in out:
+                np.testing.assert_array_equal(smp[t][ok], want[ok])
+    shared.close()
+    plain.close()
+
+
+def test_lane_merges_requests_with_their_own_seeds(qt, orc):
+    """One merged launch over trajectories of several requests (different circuits,
+    seeds and trajectory ranges): each request's samples equal the oracle's for its
+    own seed and ids."""
+    reqs = [x for x in _requests(qt, count=20, seed=13) if x[0]["n"] <= 12][:4]
+    srv = qt.Server(16 << 30, max_slots=1, small_n_max=14)
+    ids = []
+    for k, (r, f) in enumerate(reqs):
+        ids.append(srv.submit(f, seed=r["seed"], first_traj=10 * k, num_traj=3, samples_per_traj=r["samples"]))
+    for i in ids:
+        srv.wait(i, timeout_s=300)
+    assert srv.stats()["lane_launches"] <= len(reqs)
+    for k, ((r, f), i) in enumerate(zip(reqs, ids)):
+        smp, inf = srv.result(i)
+        assert inf["batched"] == 1
+        circ = qs.request_compact(r).to_circuit()
+        for t in range(3):
+            ref = orc.run_trajectory(circ, orc.DELAYED, seed=r["seed"], traj=10 * k + t)
+            if np.any(ref["margin"] <= MARGIN):
+                continue
+            want, margin = orc.sample(ref["state"], r["seed"], 10 * k + t, r["samples"])
             ok = margin > MARGIN
             np.testing.assert_array_equal(smp[t][ok], want[ok])
     srv.close()
