@@ -257,6 +257,15 @@ qt_status qt_state_apply(void* state, uint32_t n, uint32_t q, const uint32_t* qu
  * 4^q complex, row-major.  P_i = tr(K_i^dag K_i rho) (Alg. 2 step 14). */
 qt_status qt_state_reduced_density(const void* state, uint32_t n, uint32_t q,
                                    const uint32_t* qubits, double* out, void* stream);
+/* Branch probabilities of a Kraus channel on a caller-owned state (Alg. 2
+ * step 14): P_i = <psi|K_i^dag K_i|psi> for the num_ops (<= 64) operators of
+ * a channel on qubits[0..q-1] (q <= 6; ops host, num_ops matrices 2^q x 2^q
+ * row-major (re, im) FP64, basis bit b <-> qubits[b]) and N = <psi|psi>;
+ * P and N host.  q <= 3 goes through the reduced density block; q = 4..6
+ * evaluates |K_i psi|^2 per operator on the device (FP32 products, FP64
+ * carry, fixed reduction order), 16, 4 or 1 operators per pass. */
+qt_status qt_state_kraus_probabilities(const void* state, uint32_t n, uint32_t q, const uint32_t* qubits,
+                                       uint32_t num_ops, const double* ops, double* P, double* N, void* stream);
 /* Measurement of every qubit (Sec. V.C) on a caller-owned state: S
  * bitstrings x drawn with probability |psi_x|^2 / <psi|psi> (the cumulative
  * rule of qt_sample) with uniforms u01(seed, traj, 1, j); out host, S

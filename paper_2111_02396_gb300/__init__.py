@@ -13,6 +13,7 @@ from .qt import (  # noqa: F401
     Circuit, Fused, Run, QtError, load, lib_path, use_torch_allocator,
     QT_DELAYED, QT_EAGER, QT_FP32, QT_TF32X3,
     qt_state_apply, qt_state_reduced_density, qt_state_sample, qt_state_expect_z, qt_state_cdf,
+    qt_state_kraus_probabilities,
     kernel_arch,
     Batch, fuse_many, fuse_by_class, autotune_batch, Server,
 )

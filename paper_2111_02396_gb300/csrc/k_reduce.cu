@@ -32,9 +32,10 @@ __device__ __forceinline__ void block_reduce_store(double (&acc)[W], double* __r
     if (lane == 0) sm[warp][c] = v;
   }
   __syncthreads();
+  const int nw = static_cast<int>(blockDim.x >> 5);   // blocks of at most kRedThreads threads
   for (int c = threadIdx.x; c < W; c += blockDim.x) {
     double v = 0.0;
-    for (int w = 0; w < kRedThreads / 32; ++w) v += sm[w][c];
+    for (int w = 0; w < nw; ++w) v += sm[w][c];
     partial[static_cast<size_t>(blockIdx.x) * W + c] = v;
   }
 }
@@ -151,6 +152,136 @@ cudaError_t launch_rdm(const float2* psi, int n, int q, const uint32_t* qubits, 
     case 1: return rdm_q<1>(psi, n, qubits, scr, st);
     case 2: return rdm_q<2>(psi, n, qubits, scr, st);
     case 3: return rdm_q<3>(psi, n, qubits, scr, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Branch probabilities of a channel on 4..6 qubits (Alg. 2 step 14): for G
+// Kraus operators at a time, P_i = <psi|K_i^dag K_i|psi> = sum over gather
+// sets of |K_i v|^2, plus N = <psi|psi> (the 4^q-entry reduced density of
+// these widths would not fit in registers).  Each thread takes whole gather
+// sets; its set is staged column-wise in shared memory (member m of thread t
+// at v[m * blockDim + t], conflict-free) and the G operators sit in shared
+// memory.  Products and row sums in FP32; runs of kKrausChunk sets in FP32,
+// carried in FP64; fixed grid and reduction order.
+// result[0] = N, result[1 + i] = P_i.
+// ---------------------------------------------------------------------------
+constexpr int kKrausThreads = 128;
+constexpr int kKrausChunk = 16;
+
+template <int Q>
+struct KrausArgs {
+  uint64_t offs[1 << Q];
+  uint32_t ins[Q];
+  uint64_t num_sets;
+  const float2* ops;            // G matrices 2^Q x 2^Q, row-major (basis bit b <-> qubits[b])
+};
+
+template <int Q, int G>
+__global__ void __launch_bounds__(kKrausThreads) k_kraus_norms(const float2* __restrict__ psi,
+                                                               const __grid_constant__ KrausArgs<Q> a,
+                                                               double* __restrict__ partial) {
+  constexpr int D = 1 << Q, W = G + 1;
+  extern __shared__ __align__(16) float2 s_dyn[];
+  float2* sK = s_dyn;                          // G * D * D
+  float2* sv = s_dyn + G * D * D;              // D * blockDim
+  for (int i = threadIdx.x; i < G * D * D; i += blockDim.x) sK[i] = a.ops[i];
+  __syncthreads();
+  double acc[W];
+  float f[W];
+#pragma unroll
+  for (int c = 0; c < W; ++c) { acc[c] = 0.0; f[c] = 0.f; }
+  int cnt = 0;
+  const int t = threadIdx.x, bd = blockDim.x;
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < a.num_sets;
+       i += stride) {
+    uint64_t base = i;
+#pragma unroll
+    for (int b = 0; b < Q; ++b) {
+      const uint32_t s = a.ins[b];
+      base = ((base >> s) << (s + 1)) | (base & ((1ull << s) - 1ull));
+    }
+    for (int m = 0; m < D; ++m) {
+      const float2 v = __ldg(psi + base + a.offs[m]);
+      sv[m * bd + t] = v;
+      f[0] = fmaf(v.x, v.x, fmaf(v.y, v.y, f[0]));
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const float2* K = sK + g * D * D;
+      float row = 0.f;
+      for (int j = 0; j < D; ++j) {
+        float wr = 0.f, wi = 0.f;
+#pragma unroll 8
+        for (int m = 0; m < D; ++m) {
+          const float2 k = K[j * D + m];
+          const float2 v = sv[m * bd + t];
+          wr = fmaf(k.x, v.x, fmaf(-k.y, v.y, wr));
+          wi = fmaf(k.x, v.y, fmaf(k.y, v.x, wi));
+        }
+        row = fmaf(wr, wr, fmaf(wi, wi, row));
+      }
+      f[1 + g] += row;
+    }
+    if (++cnt == kKrausChunk) {
+#pragma unroll
+      for (int k = 0; k < W; ++k) { acc[k] += static_cast<double>(f[k]); f[k] = 0.f; }
+      cnt = 0;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < W; ++k) acc[k] += static_cast<double>(f[k]);
+  block_reduce_store<W>(acc, partial);
+}
+
+template <int Q, int G>
+static cudaError_t kraus_norms_q(const float2* psi, int n, const uint32_t* qubits, const float2* ops_dev,
+                                 const Scratch& scr, cudaStream_t st) {
+  constexpr int D = 1 << Q;
+  KrausArgs<Q> a;
+  uint32_t s[Q];
+  for (int b = 0; b < Q; ++b) s[b] = qubits[b];
+  for (int i = 1; i < Q; ++i)
+    for (int j = i; j > 0 && s[j - 1] > s[j]; --j) { const uint32_t t = s[j]; s[j] = s[j - 1]; s[j - 1] = t; }
+  for (int b = 0; b < Q; ++b) a.ins[b] = s[b];
+  for (int m = 0; m < D; ++m) {
+    uint64_t o = 0;
+    for (int b = 0; b < Q; ++b)
+      if ((m >> b) & 1) o |= 1ull << qubits[b];
+    a.offs[m] = o;
+  }
+  a.num_sets = 1ull << (n - Q);
+  a.ops = ops_dev;
+  const size_t smem = sizeof(float2) * (static_cast<size_t>(G) * D * D + static_cast<size_t>(D) * kKrausThreads);
+  static PerDevice setup;
+  const int grid = setup.get([smem] {
+    if (cudaFuncSetAttribute(k_kraus_norms<Q, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(smem)) != cudaSuccess)
+      return 0;
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_kraus_norms<Q, G>, kKrausThreads, smem);
+    const int g = sm_count() * (occ > 0 ? occ : 1);
+    return g < kMaxRedBlocks ? g : kMaxRedBlocks;
+  });
+  if (grid <= 0) return cudaErrorInvalidConfiguration;
+  const uint64_t need = (a.num_sets + kKrausThreads - 1) / kKrausThreads;
+  const int g = static_cast<int>(need < static_cast<uint64_t>(grid) ? need : grid);
+  k_kraus_norms<Q, G><<<g, kKrausThreads, smem, st>>>(psi, a, scr.partial);
+  k_finalize<<<1, 64, 0, st>>>(scr.partial, g, G + 1, scr.result);
+  return cudaGetLastError();
+}
+
+int kraus_group(int q) { return q <= 4 ? 16 : (q == 5 ? 4 : 1); }
+
+cudaError_t launch_kraus_norms(const float2* psi, int n, int q, const uint32_t* qubits, int nops,
+                               const float2* ops_dev, const Scratch& scr, cudaStream_t st) {
+  if (q > n || nops != kraus_group(q)) return cudaErrorInvalidValue;
+  switch (q) {
+    case 4: return kraus_norms_q<4, 16>(psi, n, qubits, ops_dev, scr, st);
+    case 5: return kraus_norms_q<5, 4>(psi, n, qubits, ops_dev, scr, st);
+    case 6: return kraus_norms_q<6, 1>(psi, n, qubits, ops_dev, scr, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -58,6 +58,13 @@ cudaError_t launch_apply(float2* psi, int n, int k, const uint32_t* targets, con
 // rho (4^q doubles, layout of rdm_unpack) of qubits Q into scr.result
 cudaError_t launch_rdm(const float2* psi, int n, int q, const uint32_t* qubits, const Scratch& scr,
                        cudaStream_t st);
+// Channels on 4..6 qubits: N and P_i = |K_i psi|^2 for kraus_group(q)
+// operators (16, 4, 1 for q = 4, 5, 6; pad with zero matrices) into
+// scr.result[0] (N) and scr.result[1..]; ops_dev: the operators, 2^q x 2^q
+// row-major complex64 in device memory, basis bit b <-> qubits[b]
+int kraus_group(int q);
+cudaError_t launch_kraus_norms(const float2* psi, int n, int q, const uint32_t* qubits, int nops,
+                               const float2* ops_dev, const Scratch& scr, cudaStream_t st);
 // N = <psi|psi> and sum |psi_x|^2 (-1)^popc(x&mask) for nm <= 16 masks into scr.result[0..nm]
 cudaError_t launch_expect(const float2* psi, int n, int nm, const uint64_t* masks,
                           const Scratch& scr, cudaStream_t st);

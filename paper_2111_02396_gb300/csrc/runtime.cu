@@ -527,11 +527,46 @@ struct Controller {
     return QT_OK;
   }
 
+  // Channels on 4..6 qubits: P_i = |K_i psi|^2 on the device, kraus_group(q)
+  // operators per pass (zero matrices pad the last group); N from the same pass.
+  DevBuf kbuf;
+  std::vector<float2> ktmp;
+  qt_status kraus_probabilities(const float2* psi, const Op& op, double& N, double* P) {
+    const int q = static_cast<int>(op.q), D = 1 << q, G = kraus_group(q);
+    const size_t mat = static_cast<size_t>(D) * D;
+    if (kbuf.bytes < sizeof(float2) * G * mat && !kbuf.alloc(sizeof(float2) * G * mat, R.st))
+      return set_error(QT_ERR_OUT_OF_MEMORY, "Kraus operator buffer");
+    for (uint32_t g0 = 0; g0 < op.num_ops; g0 += static_cast<uint32_t>(G)) {
+      ktmp.assign(G * mat, make_float2(0.f, 0.f));
+      for (uint32_t j = 0; j < static_cast<uint32_t>(G) && g0 + j < op.num_ops; ++j) {
+        const cd* K = op.kraus_op(g0 + j);
+        for (size_t e = 0; e < mat; ++e)
+          ktmp[j * mat + e] = make_float2(static_cast<float>(K[e].real()), static_cast<float>(K[e].imag()));
+      }
+      QT_CUDA(cudaMemcpyAsync(kbuf.p, ktmp.data(), sizeof(float2) * G * mat, cudaMemcpyHostToDevice, R.st),
+              "cudaMemcpyAsync(Kraus operators)");
+      QT_CUDA(launch_kraus_norms(psi, static_cast<int>(R.n), q, op.qubits, G, kbuf.as<float2>(), R.scr.s, R.st),
+              "Kraus probability kernel launch");
+      QT_CUDA(cudaMemcpyAsync(pinned, R.scr.s.result, sizeof(double) * (G + 1), cudaMemcpyDeviceToHost, R.st),
+              "cudaMemcpyAsync(probabilities)");
+      QT_CUDA(cudaStreamSynchronize(R.st), "cudaStreamSynchronize(probabilities)");
+      R.stats.h2d_bytes += sizeof(float2) * G * mat;
+      R.stats.d2h_bytes += sizeof(double) * (G + 1);
+      R.stats.kernel_launches += 2;
+      N = pinned[0];
+      for (uint32_t j = 0; j < static_cast<uint32_t>(G) && g0 + j < op.num_ops; ++j) P[g0 + j] = pinned[1 + j];
+    }
+    R.stats.prob_passes++;
+    return QT_OK;
+  }
+
   // probability pass of channel op `oi`: returns N and P[0..num_ops)
   qt_status probabilities(const float2* psi, uint32_t oi, double& N, double* P) {
     const Op& op = c.ops[oi];
-    if (op.q > static_cast<uint32_t>(kRdmMaxQ))
-      return set_error(QT_ERR_UNSUPPORTED, "channel on %u qubits: probability pass supports <= 3", op.q);
+    if (op.q > static_cast<uint32_t>(kRdmMaxQ)) {
+      if (op.q > R.n) return set_error(QT_ERR_INVALID_ARG, "channel on %u qubits of a %u-qubit state", op.q, R.n);
+      return kraus_probabilities(psi, op, N, P);
+    }
     QT_CUDA(launch_rdm(psi, static_cast<int>(R.n), static_cast<int>(op.q), op.qubits, R.scr.s, R.st),
             "probability kernel launch");
     const int W = 1 << (2 * op.q);
@@ -1066,6 +1101,69 @@ qt_status qt_state_reduced_density(const void* state, uint32_t n, uint32_t q, co
   QT_CUDA(cudaMemcpyAsync(r, scr.s.result, sizeof(double) << (2 * q), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
   QT_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
   rdm_unpack(static_cast<int>(q), r, out);
+  return QT_OK;
+}
+
+qt_status qt_state_kraus_probabilities(const void* state, uint32_t n, uint32_t q, const uint32_t* qubits,
+                                       uint32_t num_ops, const double* ops, double* P, double* N, void* stream) {
+  clear_error();
+  qt_status s = check_state(state, n, "qt_state_kraus_probabilities");
+  if (s != QT_OK) return s;
+  if (q < 1 || q > n || q > QT_MAX_OP_QUBITS)
+    return set_error(QT_ERR_UNSUPPORTED, "qt_state_kraus_probabilities: q=%u (1..min(n,6))", q);
+  if (num_ops < 1 || num_ops > 64 || !ops || !P || !N)
+    return set_error(QT_ERR_INVALID_ARG, "qt_state_kraus_probabilities: NULL argument or num_ops outside 1..64");
+  s = check_qubits(n, q, qubits, "qt_state_kraus_probabilities");
+  if (s != QT_OK) return s;
+  const int D = 1 << q;
+  const size_t mat = static_cast<size_t>(D) * D;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ScratchBufs scr;
+  if (!scr.alloc(1, st)) return set_error(QT_ERR_OUT_OF_MEMORY, "qt_state_kraus_probabilities: scratch");
+  if (q <= kRdmMaxQ) {                     // P_i = tr(K_i^dag K_i rho) from the reduced density
+    QT_CUDA(launch_rdm(static_cast<const float2*>(state), static_cast<int>(n), static_cast<int>(q), qubits, scr.s, st),
+            "qt_state_kraus_probabilities");
+    double r[64], rho[2 * 64];
+    QT_CUDA(cudaMemcpyAsync(r, scr.s.result, sizeof(double) << (2 * q), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+    QT_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    rdm_unpack(static_cast<int>(q), r, rho);
+    *N = 0.0;
+    for (int b = 0; b < D; ++b) *N += rho[2 * (b * D + b)];
+    for (uint32_t i = 0; i < num_ops; ++i) {
+      const double* K = ops + 2 * mat * i;
+      double acc = 0.0;                    // sum_{a,b} (K^dag K)[a][b] rho[b][a]
+      for (int a = 0; a < D; ++a)
+        for (int b = 0; b < D; ++b) {
+          cd m(0.0, 0.0);
+          for (int j = 0; j < D; ++j)
+            m += std::conj(cd(K[2 * (j * D + a)], K[2 * (j * D + a) + 1])) * cd(K[2 * (j * D + b)], K[2 * (j * D + b) + 1]);
+          acc += (m * cd(rho[2 * (b * D + a)], rho[2 * (b * D + a) + 1])).real();
+        }
+      P[i] = acc;
+    }
+    return QT_OK;
+  }
+  const int G = kraus_group(static_cast<int>(q));
+  DevBuf kd;
+  if (!kd.alloc(sizeof(float2) * G * mat, st)) return set_error(QT_ERR_OUT_OF_MEMORY, "qt_state_kraus_probabilities: operators");
+  std::vector<float2> tmp;
+  for (uint32_t g0 = 0; g0 < num_ops; g0 += static_cast<uint32_t>(G)) {
+    tmp.assign(G * mat, make_float2(0.f, 0.f));
+    for (uint32_t j = 0; j < static_cast<uint32_t>(G) && g0 + j < num_ops; ++j)
+      for (size_t e = 0; e < mat; ++e) {
+        const double* K = ops + 2 * (mat * (g0 + j) + e);
+        tmp[j * mat + e] = make_float2(static_cast<float>(K[0]), static_cast<float>(K[1]));
+      }
+    QT_CUDA(cudaMemcpyAsync(kd.p, tmp.data(), sizeof(float2) * G * mat, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
+    QT_CUDA(launch_kraus_norms(static_cast<const float2*>(state), static_cast<int>(n), static_cast<int>(q), qubits, G,
+                               kd.as<float2>(), scr.s, st),
+            "qt_state_kraus_probabilities");
+    double r[17];
+    QT_CUDA(cudaMemcpyAsync(r, scr.s.result, sizeof(double) * (G + 1), cudaMemcpyDeviceToHost, st), "cudaMemcpyAsync");
+    QT_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    *N = r[0];
+    for (uint32_t j = 0; j < static_cast<uint32_t>(G) && g0 + j < num_ops; ++j) P[g0 + j] = r[1 + j];
+  }
   return QT_OK;
 }
 

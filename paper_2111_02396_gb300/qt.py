@@ -126,7 +126,7 @@ EXPORTS = [
     "qt_circuit_destroy", "qt_fused_destroy", "qt_run_destroy", "qt_last_error",
     "qt_fused_info", "qt_fused_gate", "qt_channel_lower_bounds", "qt_kernel_arch",
     "qt_state_apply", "qt_state_reduced_density", "qt_state_sample", "qt_state_expect_z",
-    "qt_state_cdf", "qt_state_reduced_density_noalloc",
+    "qt_state_cdf", "qt_state_kraus_probabilities", "qt_state_reduced_density_noalloc",
     "qt_fuse_many", "qt_batch_create", "qt_batch_run", "qt_batch_samples", "qt_batch_kraus_indices",
     "qt_batch_state", "qt_batch_stats", "qt_batch_destroy", "qt_batch_autotune",
     "qt_server_create", "qt_server_submit", "qt_server_poll", "qt_server_wait", "qt_server_cancel",
@@ -174,6 +174,7 @@ def load(build_if_missing: bool = True):
             "qt_state_sample": [P, u32, u64, u64, u32, P, P, P],
             "qt_state_expect_z": [P, u32, u32, P, P, P],
             "qt_state_cdf": [P, u32, P, P],
+            "qt_state_kraus_probabilities": [P, u32, u32, P, u32, P, P, P, P],
             "qt_state_reduced_density_noalloc": [P, u32, u32, P, P, P],
             "qt_fuse_many": [u32, P, u32, u32, P],
             "qt_batch_create": [u32, P, P],
@@ -470,6 +471,18 @@ def qt_state_sample(state_ptr, n, seed, traj, S, readout_error=None, stream=None
     _check(load().qt_state_sample(state_ptr, n, seed, traj, S, _ptr(out), _ptr(ro) if ro is not None else None,
                                   stream))
     return out[:S]
+
+
+def qt_state_kraus_probabilities(state_ptr, n, qubits, Ks, stream=None):
+    """(P[num_ops], N): P_i = <psi|K_i^dag K_i|psi> of the Kraus operators Ks
+    (complex [num_ops, 2^q, 2^q]) on qubits, and N = <psi|psi>."""
+    q = np.ascontiguousarray(qubits, dtype=np.uint32)
+    K = np.ascontiguousarray(np.asarray(Ks, dtype=np.complex128)).view(np.float64)
+    P = np.zeros(len(Ks))
+    N = C.c_double()
+    _check(load().qt_state_kraus_probabilities(state_ptr, n, len(q), _ptr(q), len(Ks), _ptr(K), _ptr(P),
+                                               C.byref(N), stream))
+    return P, N.value
 
 
 def kernel_arch():

@@ -97,6 +97,30 @@ def test_apply_tf32x3_every_pattern(qt, orc, n, k):
         assert rel_l2(d.cpu().numpy(), want) < TC_L2, (qubits, rel_l2(d.cpu().numpy(), want))
 
 
+LOW_RUN_PATTERNS = [
+    [0, 1, 2, 3, 4, 5], [0, 1, 6, 7, 8, 9], [1, 2, 3, 9, 10, 11], [3, 4, 5, 11, 12, 13],
+    [0, 1, 8, 9, 16, 17], [1, 2, 3, 4, 10, 11], [1, 2, 9, 10, 17, 18], [0, 1, 2, 3, 8, 9],
+    [0, 1, 2, 3], [0, 1, 8, 9], [1, 2, 9, 10], [0, 1, 2, 3, 4], [0, 1, 2, 8, 9], [1, 2, 3, 9, 10],
+]
+
+
+def test_apply_tf32x3_low_target_runs(qt, orc):
+    """Target patterns whose gather sets are aligned runs of low amplitudes (the
+    6-qubit gates of the 32-qubit precision workload whose converter reads conflict
+    in shared memory, and 4- and 5-qubit analogues), with and without high targets,
+    against the oracle."""
+    n = 20
+    rng = np.random.default_rng(77)
+    for qubits in LOW_RUN_PATTERNS:
+        k = len(qubits)
+        U = qs.random_unitary(1 << k, rng)
+        psi = random_state(n, k + 40)
+        d = to_device(psi)
+        qt.qt_state_apply(d.data_ptr(), n, qubits, U, precision=qt.QT_TF32X3)
+        want = orc.apply(psi.astype(np.complex128), qubits, U)
+        assert rel_l2(d.cpu().numpy(), want) < TC_L2, (qubits, rel_l2(d.cpu().numpy(), want))
+
+
 @pytest.mark.parametrize("n", [13, 17])
 def test_apply_k6_fp32_every_pattern(qt, orc, n):
     """6-qubit fused gates on CUDA cores (the FP32 comparator of the TF32x3 path)."""
@@ -153,6 +177,27 @@ def test_probabilities_from_reduced_density(qt, orc, n, q):
         P_orc = orc.kraus_norms(psi.astype(np.complex128), qubits, Ks)
         np.testing.assert_allclose(P_gpu, P_orc, rtol=1e-6, atol=1e-9)
         assert abs(np.trace(rho).real - orc.norm2(psi.astype(np.complex128))) < 1e-6
+
+
+@pytest.mark.parametrize("n,q,nops", [(8, 4, 3), (9, 4, 17), (12, 5, 5), (13, 6, 2), (6, 6, 3), (20, 4, 4),
+                                      (4, 2, 5)])
+def test_kraus_probabilities(qt, orc, n, q, nops):
+    """P_i = <psi|K_i^dag K_i|psi> of random Kraus channels on 2..6 qubits (17
+    operators on 4 qubits take two passes of 16) against the FP64 oracle, N against
+    <psi|psi>, and completeness sum_i P_i = N.  Tolerance: each |K_i v|^2 row is an
+    FP32 sum of at most 64 products (rounding ~ 64 * 2^-24 ~ 4e-6 of the row), so
+    rtol 2e-5 with an absolute floor of 1e-6 N."""
+    psi = random_state(n, 21 + q) * np.float32(1.1)
+    d = to_device(psi)
+    rng = np.random.default_rng([n, q, nops])
+    qubits = [int(x) for x in rng.choice(n, q, replace=False)]
+    Ks = qs.circuits.random_kraus(1 << q, nops, rng)
+    P, N = qt.qt_state_kraus_probabilities(d.data_ptr(), n, qubits, Ks)
+    p64 = psi.astype(np.complex128)
+    N_orc = orc.norm2(p64)
+    np.testing.assert_allclose(P, orc.kraus_norms(p64, qubits, Ks), rtol=2e-5, atol=1e-6 * N_orc)
+    assert abs(N - N_orc) <= 1e-6 * N_orc
+    assert abs(P.sum() - N) <= 2e-5 * N
 
 
 @pytest.mark.parametrize("n", [1, 6, 8, 9, 10, 15, 22])

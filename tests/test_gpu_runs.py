@@ -246,6 +246,30 @@ def test_shared_prefix_equals_per_trajectory_loop(qt):
     assert a.stats()["fused_passes"] < b.stats()["fused_passes"]
 
 
+@pytest.mark.parametrize("q,n,k", [(4, 10, 4), (4, 12, 5), (5, 13, 5), (6, 13, 6)])
+def test_wide_kraus_channels_in_stage_two(qt, orc, q, n, k):
+    """Random Kraus channels on 4..6 qubits between random gates.  Their lower
+    bounds are small, so most draws go to stage 2 and the probability pass runs on
+    |K_i psi|^2 on the device: branch records (stage 2 included), states and
+    samples against the oracle."""
+    rng = np.random.default_rng([0x4b, q, n])
+    c = qs.Circuit(n)
+    m = 0
+    for layer in range(4):
+        for j in range(n):
+            c.gate(qs.random_unitary(2, rng), (j,), m)
+        m += 1
+        for j in range(layer % 2, n - 1, 2):
+            c.gate(qs.CZ, (j, j + 1), m)
+        m += 1
+        qubits = tuple(int(x) for x in rng.choice(n, q, replace=False))
+        c.kraus(qs.circuits.random_kraus(1 << q, 3, rng), qubits, m)
+        m += 1
+    run, ref = compare_run(qt, orc, c, 6, k=k, mode=qt.QT_DELAYED, seed=q, S=60, masks=[1, (1 << n) - 1])
+    assert np.sum(ref["stage"] == 2) > 0
+    assert run.stats()["flushes"] == int(np.sum(ref["stage"] == 2))
+
+
 def test_mixture_only_circuit_never_flushes(qt, orc):
     circ = qs.config3_circuit(rows=2, cols=5, depth=10, p=0.05)
     run, _ = compare_run(qt, orc, circ, 8, k=4, mode=qt.QT_DELAYED, S=50)
