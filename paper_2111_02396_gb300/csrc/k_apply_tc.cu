@@ -54,7 +54,8 @@ constexpr int kThreads = 320;           // 10 warps
 constexpr int kTileSets = 128;          // M
 constexpr int kMaxChunkReals = 64;      // K per A slot (up to 32 members)
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kSpinLimit = 1u << 22;   // x ~0.5 us nanosleep -> ~2 s bound
+constexpr uint32_t kSpinLimit = 1u << 21;   // x <= 1 us suspend per try -> ~2 s bound
+constexpr uint32_t kSuspendNs = 1000;       // suspend-time hint of one try_wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -68,14 +69,17 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// one bounded try: the thread is suspended until the phase completes or the
+// hint (ns) runs out, so a waiter wakes when its data lands instead of after
+// a fixed sleep
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.b32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
       : "memory");
   return ok != 0;
 }
@@ -85,7 +89,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 __device__ __forceinline__ bool mbar_drain(uint64_t* bar, uint32_t parity, int* err, int code) {
   for (uint32_t it = 0; it < kSpinLimit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-    __nanosleep(256);
   }
   atomicOr(err, code);
   return false;
@@ -97,7 +100,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
   for (uint32_t it = 0; it < kSpinLimit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*reinterpret_cast<volatile int*>(err)) return false;
-    __nanosleep(256);
   }
   atomicOr(err, code);
   return false;
