@@ -96,6 +96,14 @@ def test_batch_global_memory_states_match_oracle(qt, orc, k, tg):
     assert b.stats()["flushes"] > 0
 
 
+def test_batch_largest_states_match_oracle(qt, orc):
+    """The largest states the batched form accepts (19 and 20 qubits: 4 and 8 MiB slots of
+    global memory per CTA), with forced flushes, against the oracle."""
+    ccs = [_noisy(n, 4, s, 0.08) for s, n in enumerate([19, 20, 20, 8])]
+    b, _ = check_batch(qt, orc, ccs, 3, seed=11, first=900, S=64, threads=512)
+    assert b.stats()["flushes"] > 0
+
+
 def test_batch_per_class_widths_match_oracle(qt, orc):
     """Shared-memory states fused to k = 2 and global-memory states to k = 4 in one
     batch (the autotuner's per-class choice), against the oracle."""
