@@ -246,8 +246,9 @@ def test_shared_prefix_equals_per_trajectory_loop(qt):
     assert a.stats()["fused_passes"] < b.stats()["fused_passes"]
 
 
-@pytest.mark.parametrize("q,n,k", [(4, 10, 4), (4, 12, 5), (5, 13, 5), (6, 13, 6)])
-def test_wide_kraus_channels_in_stage_two(qt, orc, q, n, k):
+@pytest.mark.parametrize("q,n,k,mode", [(4, 10, 4, "delayed"), (4, 12, 5, "delayed"), (5, 13, 5, "delayed"),
+                                        (6, 13, 6, "delayed"), (4, 10, 4, "eager"), (5, 13, 6, "eager")])
+def test_wide_kraus_channels_in_stage_two(qt, orc, q, n, k, mode):
     """Random Kraus channels on 4..6 qubits between random gates.  Their lower
     bounds are small, so most draws go to stage 2 and the probability pass runs on
     |K_i psi|^2 on the device: branch records (stage 2 included), states and
@@ -265,9 +266,12 @@ def test_wide_kraus_channels_in_stage_two(qt, orc, q, n, k):
         qubits = tuple(int(x) for x in rng.choice(n, q, replace=False))
         c.kraus(qs.circuits.random_kraus(1 << q, 3, rng), qubits, m)
         m += 1
-    run, ref = compare_run(qt, orc, c, 6, k=k, mode=qt.QT_DELAYED, seed=q, S=60, masks=[1, (1 << n) - 1])
+    m = qt.QT_DELAYED if mode == "delayed" else qt.QT_EAGER
+    run, ref = compare_run(qt, orc, c, 6, k=k, mode=m, seed=q, S=60, masks=[1, (1 << n) - 1])
     assert np.sum(ref["stage"] == 2) > 0
     assert run.stats()["flushes"] == int(np.sum(ref["stage"] == 2))
+    if mode == "eager":                      # every channel evaluated
+        assert run.stats()["prob_passes"] == 6 * 4
 
 
 def test_mixture_only_circuit_never_flushes(qt, orc):
