@@ -76,7 +76,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
             if err.strip():
                 print(err)
     tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *[o for o, _ in results],
+    # -ldl: the NVTX trace ranges load a profiler's injection library on demand
+    cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *[o for o, _ in results], "-ldl",
            "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

@@ -1110,6 +1110,7 @@ qt_status qt_batch_create(uint32_t num, const qt_fused* const* fused, qt_batch**
 
 qt_status qt_batch_run(qt_batch* b, const qt_batch_params* p) {
   clear_error();
+  TraceRange tr("qt batched run");
   if (!b || !p) return set_error(QT_ERR_INVALID_ARG, "qt_batch_run: NULL argument");
   if (p->samples_per_traj > 1u << 20) return set_error(QT_ERR_INVALID_ARG, "qt_batch_run: samples_per_traj too large");
   const uint32_t threads = p->threads ? p->threads : 512;
@@ -1378,6 +1379,7 @@ qt_status lane_create(uint32_t max_n, void* stream, BatchLane** out) {
 void lane_destroy(BatchLane* l) { delete l; }
 
 qt_status lane_run(BatchLane* L, uint32_t num, const LaneTraj* tr, uint64_t* samples, uint32_t* flushes) {
+  TraceRange range("qt merged batched launch");
   if (!L || !tr || num == 0) return set_error(QT_ERR_INVALID_ARG, "lane_run: NULL argument or no trajectories");
   qt_batch* b = &L->B;
   L->fused.resize(num);

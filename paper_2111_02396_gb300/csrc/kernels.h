@@ -5,9 +5,20 @@
 
 #include <atomic>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "qt.h"
 
 namespace qt {
+
+// NVTX range for profilers (ncu --nvtx, nsys): a named span of host work and the
+// launches it makes; costs a few ns when no tool is attached.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // A launch parameter that depends on the device (SM count, occupancy, a
 // kernel attribute set once): computed by f() the first time it is asked for

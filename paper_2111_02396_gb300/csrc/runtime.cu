@@ -532,6 +532,7 @@ struct Controller {
   DevBuf kbuf;
   std::vector<float2> ktmp;
   qt_status kraus_probabilities(const float2* psi, const Op& op, double& N, double* P) {
+    TraceRange tr("qt probability pass (wide channel)");
     const int q = static_cast<int>(op.q), D = 1 << q, G = kraus_group(q);
     const size_t mat = static_cast<size_t>(D) * D;
     if (kbuf.bytes < sizeof(float2) * G * mat && !kbuf.alloc(sizeof(float2) * G * mat, R.st))
@@ -562,6 +563,7 @@ struct Controller {
 
   // probability pass of channel op `oi`: returns N and P[0..num_ops)
   qt_status probabilities(const float2* psi, uint32_t oi, double& N, double* P) {
+    TraceRange tr("qt probability pass");
     const Op& op = c.ops[oi];
     if (op.q > static_cast<uint32_t>(kRdmMaxQ)) {
       if (op.q > R.n) return set_error(QT_ERR_INVALID_ARG, "channel on %u qubits of a %u-qubit state", op.q, R.n);
@@ -668,6 +670,7 @@ struct Controller {
   }
 
   qt_status trajectory(uint32_t t, float2* psi) {
+    TraceRange tr("qt trajectory");
     Stage1 s1;
     stage1(t, s1);
     return run_from(t, psi, s1, 0);
@@ -691,6 +694,7 @@ struct Controller {
   // only the boundaries of the fused pieces differ (the piece that straddles
   // a divergence point is split, as at a flush point).
   qt_status run_shared(float2* shared, float2* work, uint64_t* d_samples) {
+    TraceRange tr("qt trajectories sharing their prefix");
     const uint32_t T = R.T, nch = R.nch;
     const uint32_t nops = static_cast<uint32_t>(c.ops.size());
     std::vector<Stage1> plan(T);
@@ -742,6 +746,7 @@ struct Controller {
   }
 
   qt_status measure(uint32_t t, const float2* psi, uint64_t* d_samples) {
+    TraceRange tr("qt measure");
     const uint64_t traj = R.p.first_traj + t;
     const uint32_t M = static_cast<uint32_t>(R.masks.size());
     double N = 0.0;
