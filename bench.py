@@ -492,8 +492,9 @@ def batched_form(steps=3, warmup=2, num=8192, plain_stride=32, uuid=None):
         "amplitude_updates_per_s": float(np.sum(nf * amps)) / med_s,
         "effective_bandwidth": {"achieved": eff_gbs, "peak": peak, "unit": "GB/s", "frac": eff_gbs / peak,
                                 "peak_kind": peak_kind,
-                                "note": "algorithmic bytes (16 B x 2^n per fused pass) / kernel time; states of "
-                                        "<= 2^14 amplitudes live in shared memory, so this is not an HBM figure"},
+                                "note": "algorithmic bytes (16 B x 2^n per fused gate, those folded into the "
+                                        "product-state start included) / kernel time; states of <= 2^14 "
+                                        "amplitudes live in shared memory, so this is not an HBM figure"},
         "l2_err_max": max(errs) if errs else None,
         "l2_err_sample": f"{len(errs)} trajectories (2 of each n in 8, 10, .., 18) against the FP64 oracle",
         "autotune_ms": {f"{c}_k{k}_t{t}": v for (c, k, t), v in table.items()},
@@ -503,6 +504,8 @@ def batched_form(steps=3, warmup=2, num=8192, plain_stride=32, uuid=None):
                                    f"samples), FP64 oracle, {t_orc:.1f} s"},
         "host_s": {"generate": t_gen, "create": t_create, "autotune": t_tune, "fuse": t_fuse, "pack": t_pack},
         "flushes_per_traj": st["flushes"] / num,
+        "fused_gates_per_traj": float(np.mean(nf)),
+        "folded_pieces_per_traj": st["folded_pieces"] / num,
         "clocks": clocks,
     }
 

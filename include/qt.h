@@ -298,7 +298,7 @@ qt_status qt_fuse_many(uint32_t num, const qt_circuit* const* circuits, uint32_t
                        uint32_t threads, qt_fused** out);
 
 /* Pack num fused circuits (1..20 qubits, ops on <= 2 qubits, fused width
- * <= 4) into device tables for the batched kernel; trajectory i of the batch
+ * <= 6) into device tables for the batched kernel; trajectory i of the batch
  * runs fused[i].  Distinct operator sets are stored once.  The fused handles
  * may be destroyed afterwards.  Errors: QT_ERR_INVALID_ARG,
  * QT_ERR_UNSUPPORTED, QT_ERR_OUT_OF_MEMORY, QT_ERR_CUDA. */
@@ -332,6 +332,7 @@ typedef struct {
   uint32_t num_traj, num_channels;
   uint64_t total_amps, fused_gates, gate_ops, flushes;
   double device_ms;            /* device time of the last run (events) */
+  uint64_t folded_pieces;      /* pieces folded into the product-state start (last run) */
 } qt_batch_stats_t;
 qt_status qt_batch_stats(const qt_batch* b, qt_batch_stats_t* out);
 void qt_batch_destroy(qt_batch* b);

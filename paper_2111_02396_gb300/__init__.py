@@ -15,5 +15,5 @@ from .qt import (  # noqa: F401
     qt_state_apply, qt_state_reduced_density, qt_state_sample, qt_state_expect_z, qt_state_cdf,
     qt_state_kraus_probabilities,
     kernel_arch,
-    Batch, fuse_many, fuse_by_class, autotune_batch, Server,
+    Batch, fuse_many, fuse_by_class, autotune_batch, Server, SMEM_N_MAX,
 )

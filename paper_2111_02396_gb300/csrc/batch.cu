@@ -9,15 +9,18 @@
 //   - one CTA per SM takes trajectories from an atomic counter, largest
 //     state first;
 //   - a state of up to 2^14 amplitudes lives in the CTA's shared memory;
-//     larger states live in a per-CTA slot of global memory (up to 2^18
-//     amplitudes, 304 MB over 152 CTAs, so they stream from DRAM, and each
-//     thread keeps 16 amplitude loads in flight to cover the latency);
+//     larger states live in a per-CTA slot of global memory (up to 2^20
+//     amplitudes, so they stream from DRAM, and each thread keeps 16
+//     amplitude loads in flight to cover the latency);
 //   - stage 1 of Alg. 2 for every channel is decided on the device with the
 //     same Philox4x32-10 draws as the plain loop; stage-2 flush points cut
 //     the circuit into segments exactly as in the plain loop, and within a
 //     segment a fused gate whose slots all hold their default operator uses
-//     its precomputed matrix while any other piece applies its member
-//     operations one by one;
+//     its precomputed matrix while any other piece has its members in the
+//     segment composed into one matrix in shared memory;
+//   - on global-memory states the first segment starts from a product
+//     state: every piece that is first on its qubits is folded into the
+//     initial state instead of making a pass of its own;
 //   - the probability pass, stage 2, and bitstring sampling run in the CTA.
 // Host side: circuits are fused on a thread pool (qt_fuse_many) and packed
 // once into device tables with every distinct operator set stored once;
@@ -45,6 +48,9 @@ namespace bt {
 constexpr int kMaxW = 6;            // widest fused gate in the batched form
 constexpr int kSmemNMax = 14;       // states up to 2^14 amplitudes in shared memory
 constexpr int kMaxN = 20;           // widest state of the batched form
+// product-state start: sum of 2^w over the folded pieces (disjoint qubits,
+// w <= 6, n <= 20 give at most 3 * 64 + 4)
+constexpr int kFoldCols = 256;
 
 struct Traj {
   uint32_t n, gate0, ngates, op0, nops, ch0, nch, chop0;   // ch0: output offset; chop0: ch_op table offset
@@ -86,6 +92,7 @@ struct Dev {
   uint8_t* gflag;                   // per fused gate of the run: a member channel holds a non-default stage-1 choice
   uint64_t* samples;
   uint32_t* flushes;
+  uint32_t* folds;                  // pieces folded into the product-state start, per trajectory (or null)
   unsigned int* counter;
   int* err;
   const uint64_t* run;              // {seed, first_traj} of the current run (device copy)
@@ -477,6 +484,174 @@ __device__ void cta_sample(const float2* psi, int n, uint64_t seed, uint64_t tra
   }
 }
 
+// The piece of fused gate G over ops [lo, hi): its members there composed in
+// FP32 into one matrix over the gate's qubits, left in s_mat (D x D
+// row-major; identity on qubits none of them touches).  The channel decided
+// in stage 2 at the segment's start (op pend_pos) enters as its Kraus
+// operator pend_choice scaled by pend_scale; any other channel as its
+// stage-1 choice.
+__device__ __forceinline__ void cta_compose_piece(const Dev& d, const Traj& T, const Gate& G, uint32_t lo, uint32_t hi,
+                                  int pend_pos, int pend_choice, float pend_scale, float2* s_mat) {
+  const int D = 1 << G.w;
+  __syncthreads();                 // previous users of s_mat are done
+  for (int i = threadIdx.x; i < D * D; i += blockDim.x)
+    s_mat[i] = make_float2((i >> G.w) == (i & (D - 1)) ? 1.f : 0.f, 0.f);
+  for (uint32_t mi = 0; mi < G.nmem; ++mi) {
+    const uint32_t pos = d.members[G.mem0 + mi];
+    if (pos < lo || pos >= hi) continue;
+    const Op op = d.ops[T.op0 + pos];
+    const Set st = d.sets[op.set];
+    const uint32_t dd = 1u << (2 * op.q);
+    const float2* A;
+    float sc = 1.f;
+    if (op.channel < 0) {
+      A = d.fmat + st.mat;
+    } else if (static_cast<int>(pos) == pend_pos) {
+      A = d.fmat + st.kraus + pend_choice * dd;
+      sc = pend_scale;
+    } else {
+      A = d.fmat + st.mat + d.kraus[T.ch0 + op.channel] * dd;
+    }
+    int p[2] = {0, 0};
+    for (int b = 0; b < G.w; ++b) {
+      if (G.t[b] == op.q0) p[0] = b;
+      if (op.q > 1 && G.t[b] == op.q1) p[1] = b;
+    }
+    __syncthreads();               // the previous member's update is complete
+    cta_left_apply(s_mat, G.w, op.q, p, A, sc);
+  }
+}
+
+__device__ __forceinline__ uint32_t gate_mask(const Gate& G) {
+  uint32_t m = 0;
+  for (int b = 0; b < G.w; ++b) m |= 1u << G.t[b];
+  return m;
+}
+
+// Product-state start (the first segment, ops [0, hi)).  A piece none of
+// whose qubits an earlier piece of the segment touches acts on |0> of its
+// own qubits and commutes with every piece before it, so it moves to the
+// front: its column U[:, 0] becomes a factor of the initial state
+//   psi[x] = prod_f U_f[x restricted to the qubits of f, 0],
+// zero where x has a 1 on a qubit that no folded piece holds.  The qubits
+// are split at m: the factors of the pieces wholly below m form a table of
+// 2^m entries, those wholly from m up one of 2^(n-m) (both in s_mat), so an
+// amplitude is one product of two table entries, times the factors of the
+// few pieces that straddle m (m is chosen to have the fewest).  Writes the
+// whole state, marks the folded gates (gate flag 2: the pass loop of the
+// first segment skips them; a later segment treats such a gate, which the
+// flush point cut, as a composed piece) and returns their number.
+struct FoldPiece {
+  uint32_t mask;                   // its qubits
+  uint32_t gate;                   // its fused gate
+  uint16_t off;                    // its column in s_col
+  uint8_t w, q[kMaxW];             // its qubits, basis bit b <-> q[b]
+};
+constexpr uint32_t kTableAmps = 1u << (2 * kMaxW);   // s_mat holds both tables
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// factor U_f[x restricted to the qubits of f, 0]
+__device__ __forceinline__ float2 fold_factor(const FoldPiece& F, const float2* s_col, uint32_t x) {
+  uint32_t idx = 0;
+  for (int b = 0; b < F.w; ++b) idx |= ((x >> F.q[b]) & 1u) << b;
+  return s_col[F.off + idx];
+}
+
+__device__ __noinline__ int cta_product_start(const Dev& d, const Traj& T, float2* psi, uint32_t hi,
+                                              float2* s_mat, float2* s_col, FoldPiece* s_fold) {
+  __shared__ int s_split, s_nstr;
+  __shared__ uint8_t s_str[kMaxN];
+  const int tid = threadIdx.x;
+  const int n = static_cast<int>(T.n);
+  const uint32_t all = (1u << n) - 1u;
+  uint32_t touched = 0, held = 0;
+  int nf = 0, off = 0;
+  // once every qubit is touched no later piece can fold
+  for (uint32_t g = 0; g < T.ngates && touched != all; ++g) {
+    const Gate G = d.gates[T.gate0 + g];
+    if (G.minpos >= hi) continue;
+    const uint32_t gm = gate_mask(G);
+    const bool fold = !(gm & touched);
+    touched |= gm;
+    if (!fold) continue;
+    const int D = 1 << G.w;
+    const float2* col = d.fmat + G.mat;          // column 0 of the precomputed matrix, stride D
+    if (G.maxpos >= hi || d.gflag[T.gf0 + g]) {
+      cta_compose_piece(d, T, G, 0, hi, -1, 0, 1.f, s_mat);
+      __syncthreads();
+      col = s_mat;
+    }
+    for (int i = tid; i < D; i += blockDim.x) s_col[off + i] = col[i * D];
+    if (tid == 0) {
+      FoldPiece& F = s_fold[nf];
+      F.mask = gm;
+      F.gate = g;
+      F.off = static_cast<uint16_t>(off);
+      F.w = G.w;
+      for (int b = 0; b < G.w; ++b) F.q[b] = G.t[b];
+    }
+    held |= gm;
+    off += D;
+    ++nf;
+  }
+  __syncthreads();                 // every thread has read the gate flags; s_fold is complete
+  if (tid < 32) {
+    // lane c scores the split at m = c: fewest straddling pieces, then the
+    // most even tables, among the splits whose tables fit s_mat
+    const int c = tid;
+    uint32_t key = 0xffffffffu;
+    if (c <= n && (1u << c) + (1u << (n - c)) <= kTableAmps) {
+      int str = 0;
+      for (int f = 0; f < nf; ++f) str += (s_fold[f].mask & ((1u << c) - 1u)) && (s_fold[f].mask >> c);
+      key = (static_cast<uint32_t>(str) << 16) | (static_cast<uint32_t>(abs(2 * c - n)) << 5) |
+            static_cast<uint32_t>(c);
+    }
+    for (int o = 16; o > 0; o >>= 1) key = min(key, __shfl_xor_sync(0xffffffffu, key, o));
+    if (tid == 0) {
+      const int m = static_cast<int>(key & 31u);
+      s_split = m;
+      int ns = 0;
+      for (int f = 0; f < nf; ++f)
+        if ((s_fold[f].mask & ((1u << m) - 1u)) && (s_fold[f].mask >> m)) s_str[ns++] = static_cast<uint8_t>(f);
+      s_nstr = ns;
+    }
+    // mark the folded gates for the pass loop
+    for (int f = tid; f < nf; f += 32) d.gflag[T.gf0 + s_fold[f].gate] = 2;
+  }
+  __syncthreads();
+  const int m = s_split, ns = s_nstr;
+  const uint32_t lmask = (1u << m) - 1u, nlo = 1u << m, nhi = 1u << (n - m);
+  const uint32_t zero = all & ~held;                 // qubits no folded piece holds stay |0>
+  float2* t_lo = s_mat;
+  float2* t_hi = s_mat + nlo;
+  for (uint32_t y = tid; y < nlo + nhi; y += blockDim.x) {
+    const bool upper = y >= nlo;
+    const uint32_t x = upper ? (y - nlo) << m : y;   // the index bits this entry stands for
+    const uint32_t half = upper ? ~lmask : lmask;
+    float2 v = make_float2(0.f, 0.f);
+    if (!(x & zero)) {
+      v.x = 1.f;
+      for (int f = 0; f < nf; ++f)
+        if (!(s_fold[f].mask & ~half)) v = cmul(v, fold_factor(s_fold[f], s_col, x));
+    }
+    if (upper) t_hi[y - nlo] = v;
+    else t_lo[y] = v;
+  }
+  __syncthreads();
+  const uint64_t amps = 1ull << n;
+  for (uint64_t x = tid; x < amps; x += blockDim.x) {
+    const uint32_t xi = static_cast<uint32_t>(x);
+    float2 v = cmul(t_lo[xi & lmask], t_hi[xi >> m]);
+    for (int j = 0; j < ns; ++j) v = cmul(v, fold_factor(s_fold[s_str[j]], s_col, xi));
+    psi[x] = v;
+  }
+  __syncthreads();                 // the marks and the state are visible to the CTA
+  return nf;
+}
+
 __device__ __forceinline__ int decide_stage1(const Set& st, const double* pbar, double r) {
   double rr = r;
   for (uint32_t i = 0; i < st.nk; ++i) {
@@ -504,6 +679,8 @@ __global__ void __launch_bounds__(512) k_batch(const __grid_constant__ Dev d) {
   __shared__ int s_next;
   __shared__ float s_scale;
   __shared__ int s_pend_pos, s_pend_choice;
+  __shared__ float2 s_col[kFoldCols];               // columns U[:, 0] of the folded pieces
+  __shared__ FoldPiece s_fold[kMaxN];
   const int tid = threadIdx.x;
 
   for (;;) {
@@ -523,7 +700,10 @@ __global__ void __launch_bounds__(512) k_batch(const __grid_constant__ Dev d) {
     float2* psi;
     if (!GLOBAL) psi = s_state;
     else psi = d.keep ? d.arena + T.arena_off : d.arena + static_cast<uint64_t>(blockIdx.x) * d.slot_amps;
-    for (uint64_t x = tid; x < amps; x += blockDim.x) psi[x] = make_float2(x == 0 ? 1.f : 0.f, 0.f);
+    // shared-memory states start from |0...0>; global-memory states from the
+    // product state that the first segment writes (cta_product_start)
+    if (!GLOBAL)
+      for (uint64_t x = tid; x < amps; x += blockDim.x) psi[x] = make_float2(x == 0 ? 1.f : 0.f, 0.f);
     // stage 1 of every channel from its draw and the lower bounds
     for (uint32_t c = tid; c < T.nch; c += blockDim.x) {
       const Op op = d.ops[T.op0 + d.ch_op[T.chop0 + c]];
@@ -563,10 +743,22 @@ __global__ void __launch_bounds__(512) k_batch(const __grid_constant__ Dev d) {
       const uint32_t hi = fch >= 0 ? d.ch_op[T.chop0 + fch] : T.nops;
       const int pend_pos = s_pend_pos, pend_choice = s_pend_choice;
       const float pend_scale = s_scale;
-      // apply ops [lo, hi): fused gates restricted to the segment
+      // the product-state start pays on global-memory states, where a pass
+      // streams the state from DRAM; on shared-memory states (passes of a few
+      // microseconds) it measured slower than the passes it saves
+      const bool first = GLOBAL && lo == 0 && nflush == 0;
+      if constexpr (GLOBAL) {
+        if (first) {
+          const int nf = cta_product_start(d, T, psi, hi, s_mat, s_col, s_fold);
+          if (tid == 0 && d.folds) d.folds[ti] = static_cast<uint32_t>(nf);
+        }
+      }
+      // apply ops [lo, hi): fused gates restricted to the segment (in the
+      // first segment, those not folded into the initial state)
       for (uint32_t g = 0; g < T.ngates; ++g) {
         const Gate G = d.gates[T.gate0 + g];
         if (G.maxpos < lo || G.minpos >= hi) continue;
+        if (first && d.gflag[T.gf0 + g] == 2) continue;
         bool dflt = G.minpos >= lo && G.maxpos < hi && !d.gflag[T.gf0 + g];
         // the channel decided in stage 2 at this segment's start is applied as
         // its normalized Kraus operator, so the gate holding it is never default
@@ -584,34 +776,7 @@ __global__ void __launch_bounds__(512) k_batch(const __grid_constant__ Dev d) {
         // its members in [lo, hi) are composed in FP32 in shared memory into
         // one matrix over the gate's qubits (identity on qubits none of them
         // touches), then applied in one pass
-        const int D = 1 << G.w;
-        __syncthreads();                 // previous users of s_mat are done
-        for (int i = tid; i < D * D; i += blockDim.x)
-          s_mat[i] = make_float2((i >> G.w) == (i & (D - 1)) ? 1.f : 0.f, 0.f);
-        for (uint32_t mi = 0; mi < G.nmem; ++mi) {
-          const uint32_t pos = d.members[G.mem0 + mi];
-          if (pos < lo || pos >= hi) continue;
-          const Op op = d.ops[T.op0 + pos];
-          const Set st = d.sets[op.set];
-          const uint32_t dd = 1u << (2 * op.q);
-          const float2* A;
-          float sc = 1.f;
-          if (op.channel < 0) {
-            A = d.fmat + st.mat;
-          } else if (static_cast<int>(pos) == pend_pos) {
-            A = d.fmat + st.kraus + pend_choice * dd;
-            sc = pend_scale;
-          } else {
-            A = d.fmat + st.mat + d.kraus[T.ch0 + op.channel] * dd;
-          }
-          int p[2] = {0, 0};
-          for (int b = 0; b < G.w; ++b) {
-            if (G.t[b] == op.q0) p[0] = b;
-            if (op.q > 1 && G.t[b] == op.q1) p[1] = b;
-          }
-          __syncthreads();               // the previous member's update is complete
-          cta_left_apply(s_mat, G.w, op.q, p, A, sc);
-        }
+        cta_compose_piece(d, T, G, lo, hi, pend_pos, pend_choice, pend_scale, s_mat);
         int order[kMaxW];
         for (int b = 0; b < G.w; ++b) order[b] = G.t[b];
         cta_apply<GLOBAL>(psi, n, G.w, order, s_mat, 1.f, s_mat);
@@ -684,7 +849,10 @@ __global__ void __launch_bounds__(512) k_batch(const __grid_constant__ Dev d) {
       __syncthreads();
       for (uint64_t x = tid; x < amps; x += blockDim.x) d.arena[T.arena_off + x] = psi[x];
     }
-    if (tid == 0) d.flushes[ti] = nflush;
+    if (tid == 0) {
+      d.flushes[ti] = nflush;
+      if (!GLOBAL && d.folds) d.folds[ti] = 0;
+    }
   }
 }
 
@@ -753,7 +921,7 @@ struct qt_batch {
   DevMem tables, arena, outs, counter;
   uint64_t* hrun = nullptr;         // pinned {seed, first_traj}; the graph copies it to counter+16
   bt::Dev dev{};
-  size_t off_kraus = 0, off_stage = 0, off_samples = 0, off_flushes = 0, off_err = 0, off_gflag = 0;
+  size_t off_kraus = 0, off_stage = 0, off_samples = 0, off_flushes = 0, off_folds = 0, off_err = 0, off_gflag = 0;
   uint64_t total_gates = 0;         // sum of the trajectories' fused-gate counts (one flag each per run)
   uint32_t S = 0, keep = 0;
   std::vector<uint8_t> host;        // host image of the device tables
@@ -762,7 +930,7 @@ struct qt_batch {
   // results on the host
   std::vector<int32_t> kraus, stage;
   std::vector<uint64_t> samples;
-  std::vector<uint32_t> flushes;
+  std::vector<uint32_t> flushes, folds;
   double device_ms = 0.0;
   uint64_t gate_ops = 0, fused_gates = 0;
   // trajectories with states in global memory (n > 14) come first in `order`;
@@ -1132,6 +1300,7 @@ qt_status qt_batch_run(qt_batch* b, const qt_batch_params* p) {
     b->off_stage = off; off = align(off + sizeof(int32_t) * std::max<uint32_t>(b->total_ch, 1));
     b->off_samples = off; off = align(off + sizeof(uint64_t) * std::max<uint64_t>(uint64_t(b->num) * b->S, 1));
     b->off_flushes = off; off = align(off + sizeof(uint32_t) * b->num);
+    b->off_folds = off; off = align(off + sizeof(uint32_t) * b->num);
     b->off_gflag = off; off = align(off + std::max<uint64_t>(b->total_gates, 1));
     if (!b->outs.alloc(off)) return set_error(QT_ERR_OUT_OF_MEMORY, "qt_batch_run: outputs");
     uint8_t* o = static_cast<uint8_t*>(b->outs.p);
@@ -1139,6 +1308,7 @@ qt_status qt_batch_run(qt_batch* b, const qt_batch_params* p) {
     d.stage = reinterpret_cast<int32_t*>(o + b->off_stage);
     d.samples = reinterpret_cast<uint64_t*>(o + b->off_samples);
     d.flushes = reinterpret_cast<uint32_t*>(o + b->off_flushes);
+    d.folds = reinterpret_cast<uint32_t*>(o + b->off_folds);
     d.gflag = o + b->off_gflag;
     int sms = sm_count();
     const uint64_t slot = b->max_n > static_cast<uint32_t>(bt::kSmemNMax) ? (1ull << b->max_n) : 0;
@@ -1154,6 +1324,7 @@ qt_status qt_batch_run(qt_batch* b, const qt_batch_params* p) {
     b->stage.assign(b->total_ch, 0);
     b->samples.assign(static_cast<size_t>(b->num) * b->S, 0);
     b->flushes.assign(b->num, 0);
+    b->folds.assign(b->num, 0);
   }
   b->hrun[0] = p->seed;
   b->hrun[1] = p->first_traj;
@@ -1206,6 +1377,7 @@ qt_status qt_batch_run(qt_batch* b, const qt_batch_params* p) {
   if (e == cudaSuccess && b->S)
     e = cudaMemcpyAsync(b->samples.data(), d.samples, sizeof(uint64_t) * b->samples.size(), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(b->flushes.data(), d.flushes, sizeof(uint32_t) * b->num, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->folds.data(), d.folds, sizeof(uint32_t) * b->num, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   float ms = 0.f;
   if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
@@ -1273,6 +1445,9 @@ qt_status qt_batch_stats(const qt_batch* b, qt_batch_stats_t* out) {
   for (uint32_t x : b->flushes) f += x;
   out->flushes = f;
   out->device_ms = b->device_ms;
+  uint64_t fo = 0;
+  for (uint32_t x : b->folds) fo += x;
+  out->folded_pieces = fo;
   return QT_OK;
 }
 
@@ -1405,6 +1580,7 @@ qt_status lane_run(BatchLane* L, uint32_t num, const LaneTraj* tr, uint64_t* sam
   d.stage = reinterpret_cast<int32_t*>(o + o_stage);
   d.samples = reinterpret_cast<uint64_t*>(o + o_samp);
   d.flushes = reinterpret_cast<uint32_t*>(o + o_flush);
+  d.folds = nullptr;
   d.gflag = o + o_gflag;
   d.arena = static_cast<float2*>(b->arena.p);
   d.slot_amps = L->slot;

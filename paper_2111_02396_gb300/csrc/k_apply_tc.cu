@@ -132,6 +132,12 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
   return r;
 }
 
+// x = hi + lo, both TF32 (the split of the three-pass scheme)
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = to_tf32(x);
+  lo = to_tf32(x - __uint_as_float(hi));
+}
+
 // 32 consecutive 32-bit columns of this thread's lane
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
   asm volatile(
@@ -206,7 +212,11 @@ struct TcArgs {
   uint32_t lbo, sbo;         // B descriptor offsets (bytes)
 };
 
-template <int K>
+// PAIR: qubit 0 is a target (member bit 0 sits at offset 0), so members 2j
+// and 2j + 1 of a set are adjacent, 16-byte aligned amplitudes (the set's own
+// offset has bit 0 clear): they are read and written as pairs.  A template
+// parameter, so that the other patterns run the code without the branch.
+template <int K, bool PAIR>
 __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict__ psi, const __grid_constant__ TcArgs<K> a) {
   using namespace tc;
   constexpr int NM = 1 << K;                 // members per set
@@ -356,14 +366,24 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
         uint32_t hi[32], lo[32];
 #pragma unroll
         for (int half = 0; half < MPC / 16; ++half) {
+          if constexpr (PAIR) {
+            // members 2j and 2j + 1 are adjacent amplitudes: one 16-byte load
 #pragma unroll
-          for (int m = 0; m < 16; ++m) {
-            const float2 v = tb[(sbase | a.moff[c * MPC + half * 16 + m]) - tsub];
-            const uint32_t hr = to_tf32(v.x), hm = to_tf32(v.y);
-            hi[2 * m] = hr;
-            hi[2 * m + 1] = hm;
-            lo[2 * m] = to_tf32(v.x - __uint_as_float(hr));
-            lo[2 * m + 1] = to_tf32(v.y - __uint_as_float(hm));
+            for (int m = 0; m < 16; m += 2) {
+              const float4 v =
+                  *reinterpret_cast<const float4*>(tb + ((sbase | a.moff[c * MPC + half * 16 + m]) - tsub));
+              split_tf32(v.x, hi[2 * m], lo[2 * m]);
+              split_tf32(v.y, hi[2 * m + 1], lo[2 * m + 1]);
+              split_tf32(v.z, hi[2 * m + 2], lo[2 * m + 2]);
+              split_tf32(v.w, hi[2 * m + 3], lo[2 * m + 3]);
+            }
+          } else {
+#pragma unroll
+            for (int m = 0; m < 16; ++m) {
+              const float2 v = tb[(sbase | a.moff[c * MPC + half * 16 + m]) - tsub];
+              split_tf32(v.x, hi[2 * m], lo[2 * m]);
+              split_tf32(v.y, hi[2 * m + 1], lo[2 * m + 1]);
+            }
           }
           const uint32_t col = a_col0 + slot * 128 + half * 32;
           tmem_st32(tmem + lane_base + col, hi);
@@ -406,11 +426,21 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           if (cb + h >= N / 32) break;
+          if constexpr (PAIR) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const uint32_t l = sbase | a.moff[(cb + h) * 16 + j];
-            __stcs(psi + (base | a.roff[l >> a.C] | (l & rowmask)),
-                   make_float2(__uint_as_float(v[h][2 * j]), __uint_as_float(v[h][2 * j + 1])));
+            for (int j = 0; j < 16; j += 2) {
+              const uint32_t l = sbase | a.moff[(cb + h) * 16 + j];
+              __stcs(reinterpret_cast<float4*>(psi + (base | a.roff[l >> a.C] | (l & rowmask))),
+                     make_float4(__uint_as_float(v[h][2 * j]), __uint_as_float(v[h][2 * j + 1]),
+                                 __uint_as_float(v[h][2 * j + 2]), __uint_as_float(v[h][2 * j + 3])));
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const uint32_t l = sbase | a.moff[(cb + h) * 16 + j];
+              __stcs(psi + (base | a.roff[l >> a.C] | (l & rowmask)),
+                     make_float2(__uint_as_float(v[h][2 * j]), __uint_as_float(v[h][2 * j + 1])));
+            }
           }
         }
       }
@@ -482,8 +512,12 @@ static cudaError_t launch_tc_k(float2* psi, int n, const uint32_t* targets, cons
   const size_t smem = 2 * sizeof(float) * N * N + TBUF_AMPS * sizeof(float2) + 24 * sizeof(uint64_t) + 16;
   static PerDevice attr_set;
   const cudaError_t attr_err = static_cast<cudaError_t>(attr_set.get([&] {
-    return static_cast<int>(
-        cudaFuncSetAttribute(k_apply_tc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    cudaError_t e = cudaFuncSetAttribute(k_apply_tc<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_apply_tc<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               static_cast<int>(smem));
+    return static_cast<int>(e);
   }));
   if (attr_err != cudaSuccess) return attr_err;
   TcArgs<K> a;
@@ -525,7 +559,10 @@ static cudaError_t launch_tc_k(float2* psi, int n, const uint32_t* targets, cons
   a.sbo = sbo_override ? sbo_override : 128 * (N / 4);
   uint64_t grid = static_cast<uint64_t>(sm_count());
   if (grid > a.num_tiles) grid = a.num_tiles;
-  k_apply_tc<K><<<static_cast<unsigned>(grid), tc::kThreads, smem, st>>>(psi, a);
+  if (a.moff[1] == 1u)            // qubit 0 is a target (targets ascending)
+    k_apply_tc<K, true><<<static_cast<unsigned>(grid), tc::kThreads, smem, st>>>(psi, a);
+  else
+    k_apply_tc<K, false><<<static_cast<unsigned>(grid), tc::kThreads, smem, st>>>(psi, a);
   return cudaGetLastError();
 }
 

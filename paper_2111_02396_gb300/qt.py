@@ -77,7 +77,7 @@ class qt_batch_params(C.Structure):
 class qt_batch_stats_t(C.Structure):
     _fields_ = [("num_traj", C.c_uint32), ("num_channels", C.c_uint32), ("total_amps", C.c_uint64),
                 ("fused_gates", C.c_uint64), ("gate_ops", C.c_uint64), ("flushes", C.c_uint64),
-                ("device_ms", C.c_double)]
+                ("device_ms", C.c_double), ("folded_pieces", C.c_uint64)]
 
 
 class qt_server_config(C.Structure):

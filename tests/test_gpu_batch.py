@@ -5,8 +5,8 @@ the FP64 oracle run of the same circuit, seed and trajectory id (branch
 records where the margin exceeds 1e-6, final state within relative L2
 2e-5 / fidelity 1 - 1e-5, samples where the CDF margin exceeds 1e-6), and
 with the plain per-trajectory loop.  Covers states in shared memory
-(n <= 14) and in global memory (n = 15..18), forced stage-2 flushes, CUDA
-graph replay, and the autotuner.
+(n <= 14) and in global memory (n = 15..20), forced stage-2 flushes, the
+product-state start, CUDA graph replay, and the autotuner.
 """
 import numpy as np
 import pytest
@@ -113,6 +113,44 @@ def test_batch_per_class_widths_match_oracle(qt, orc):
     widths = [f.info()["max_width"] for f in fs]
     assert max(w for w, c in zip(widths, ccs) if c.num_qubits <= 14) <= 2
     assert max(w for w, c in zip(widths, ccs) if c.num_qubits > 14) == 4
+
+
+def _first_on_qubits(fused, min_n):
+    """Fused gates that are first on their qubits (none of their targets held by an
+    earlier fused gate) in the circuits of at least min_n qubits: the pieces a
+    noiseless circuit folds into its initial state."""
+    count = 0
+    for f in fused:
+        if f.circuit.num_qubits < min_n:
+            continue
+        seen = 0
+        for g in range(f.info()["num_fused"]):
+            m = sum(1 << int(q) for q in f.gate(g)["targets"])
+            count += not (m & seen)
+            seen |= m
+    return count
+
+
+def test_batch_product_state_start(qt, orc):
+    """Global-memory states (n > 14) start the first segment from a product state: a
+    piece first on its qubits is folded into the initial state as its column U[:, 0]
+    instead of making a pass.  Noiseless circuits (the whole circuit is one segment)
+    fold exactly the fused gates first on their qubits; noisy ones also fold pieces
+    composed from non-default stage-1 choices and pieces cut by the first flush
+    point.  Shared-memory states in the same batch start from |0...0>.  All against
+    the oracle."""
+    chain = qs.circuits._chain_couplings
+    clean = [qs.layered_compact(n, 5, np.random.default_rng([0x70, n]), lambda l, n=n: chain(n, l))
+             for n in (5, 9, 13, 16, 18)]
+    b, fs = check_batch(qt, orc, clean, 3, seed=2, S=32)
+    st = b.stats()
+    assert st["num_channels"] == 0 and st["flushes"] == 0
+    assert st["folded_pieces"] == _first_on_qubits(fs, qt.SMEM_N_MAX + 1) > 0
+    noisy = [qs.layered_compact(n, 6, np.random.default_rng([0x71, n]), lambda l, n=n: chain(n, l),
+                                dep1=0.3, per_gate_ad=0.1) for n in (7, 10, 14, 15, 17)]
+    b, fs = check_batch(qt, orc, noisy, 4, seed=4, first=60, S=32)
+    st = b.stats()
+    assert st["flushes"] > 0 and st["folded_pieces"] > 0
 
 
 def test_batch_equals_plain_loop(qt):
