@@ -25,6 +25,7 @@ PATTERNS = {
     "low1": lambda n, k: list(range(1, k + 1)),
     "mixed": lambda n, k: [0] + list(range(n - k + 1, n)),
     "spread": lambda n, k: [int(round(j * (n - 1) / max(k - 1, 1))) for j in range(k)],
+    "low123": lambda n, k: [1, 2, 3] + [n // 2 + j for j in range(k - 3)],
 }
 
 

@@ -132,6 +132,14 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
   return r;
 }
 
+// a wait's outcome, made the same for the whole warp when the warp then
+// exchanges values with shuffles (every lane must reach them)
+template <bool UNIFORM>
+__device__ __forceinline__ bool warp_ok(bool ok) {
+  if constexpr (UNIFORM) return __all_sync(0xffffffffu, ok);
+  else return ok;
+}
+
 // x = hi + lo, both TF32 (the split of the three-pass scheme)
 __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
   hi = to_tf32(x);
@@ -212,11 +220,24 @@ struct TcArgs {
   uint32_t lbo, sbo;         // B descriptor offsets (bytes)
 };
 
-// PAIR: qubit 0 is a target (member bit 0 sits at offset 0), so members 2j
-// and 2j + 1 of a set are adjacent, 16-byte aligned amplitudes (the set's own
-// offset has bit 0 clear): they are read and written as pairs.  A template
-// parameter, so that the other patterns run the code without the branch.
-template <int K, bool PAIR>
+// MODE selects how the converters and the epilogue move amplitudes between
+// the staged tile, TMEM and the state (a template parameter, so that each
+// target pattern runs code without the others' branches):
+//   kMemberPairs: qubit 0 is a target (member bit 0 sits at offset 0), so
+//     members 2j and 2j + 1 of a set are adjacent, 16-byte aligned
+//     amplitudes (the set's own offset has bit 0 clear): one 16-byte access
+//     each;
+//   kSetPairs: qubit 0 is not a target, so the sets of threads 2i and 2i + 1
+//     (TMEM lanes 2i, 2i + 1) differ only in amplitude bit 0: member m of both
+//     is one 16-byte chunk.  The even thread takes the chunk of member m, the
+//     odd one that of member m + 1, and one shuffle swaps the halves each
+//     needs; the epilogue writes the same chunks after the reverse swap.
+//     Half the shared-memory wavefronts and global store instructions of
+//     single 8-byte accesses where low targets make them conflict;
+//   kSingle: 8-byte accesses, one member at a time.
+constexpr int kSingle = 0, kMemberPairs = 1, kSetPairs = 2;
+
+template <int K, int MODE>
 __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict__ psi, const __grid_constant__ TcArgs<K> a) {
   using namespace tc;
   constexpr int NM = 1 << K;                 // members per set
@@ -338,6 +359,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
   } else if (warp < 4) {
     // ---------------- converters ----------------
     const uint32_t lane_base = static_cast<uint32_t>(warp * 32) << 16;
+    const bool odd = lane & 1;
     uint32_t sbase = threadIdx.x;
 #pragma unroll
     for (int b = 0; b < K; ++b) {
@@ -348,7 +370,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
     bool ok = true;
     for (uint64_t tile = blockIdx.x; tile < a.num_tiles && ok; tile += gridDim.x, ++it) {
       const uint32_t b = split ? 0u : it % NBUF;
-      if (!split && !mbar_wait(&t_full[b], (it / NBUF) & 1, a.err, 64)) break;
+      if (!split && !warp_ok<MODE == kSetPairs>(mbar_wait(&t_full[b], (it / NBUF) & 1, a.err, 64))) break;
       const float2* tb = tbuf + b * TILE_AMPS;
       for (int c = 0; c < NCHUNK; ++c, ++chunk_iter) {
         // split: this chunk half sits in ring slot chunk_iter % RING; its members'
@@ -356,17 +378,38 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
         const uint32_t rs = chunk_iter % RING;
         uint32_t tsub = 0;                   // tile offset of the staged unit's first amplitude
         if (split) {
-          if (!mbar_wait(&t_full[rs], (chunk_iter / RING) & 1, a.err, 64)) { ok = false; break; }
+          if (!warp_ok<MODE == kSetPairs>(mbar_wait(&t_full[rs], (chunk_iter / RING) & 1, a.err, 64))) {
+            ok = false;
+            break;
+          }
           tb = tbuf + rs * (TILE_AMPS / 2);
           tsub = static_cast<uint32_t>(c) * (TILE_AMPS / 2);
         }
         const uint32_t slot = chunk_iter & 1;
         const uint32_t use = chunk_iter >> 1;
-        if (use > 0 && !mbar_wait(&a_empty[slot], (use - 1) & 1, a.err, 1)) { ok = false; break; }
+        if (use > 0 && !warp_ok<MODE == kSetPairs>(mbar_wait(&a_empty[slot], (use - 1) & 1, a.err, 1))) {
+          ok = false;
+          break;
+        }
         uint32_t hi[32], lo[32];
 #pragma unroll
         for (int half = 0; half < MPC / 16; ++half) {
-          if constexpr (PAIR) {
+          if constexpr (MODE == kSetPairs) {
+#pragma unroll
+            for (int m = 0; m < 16; m += 2) {
+              const int i = c * MPC + half * 16 + m;
+              const uint32_t mo = odd ? a.moff[i + 1] : a.moff[i];
+              const float4 v = *reinterpret_cast<const float4*>(tb + (((sbase & ~1u) | mo) - tsub));
+              // even: (x, y) is its member m, (z, w) the odd thread's member m;
+              // odd: (z, w) is its member m + 1, (x, y) the even thread's
+              const float rx = __shfl_xor_sync(0xffffffffu, odd ? v.x : v.z, 1);
+              const float ry = __shfl_xor_sync(0xffffffffu, odd ? v.y : v.w, 1);
+              split_tf32(odd ? rx : v.x, hi[2 * m], lo[2 * m]);
+              split_tf32(odd ? ry : v.y, hi[2 * m + 1], lo[2 * m + 1]);
+              split_tf32(odd ? v.z : rx, hi[2 * m + 2], lo[2 * m + 2]);
+              split_tf32(odd ? v.w : ry, hi[2 * m + 3], lo[2 * m + 3]);
+            }
+          } else if constexpr (MODE == kMemberPairs) {
             // members 2j and 2j + 1 are adjacent amplitudes: one 16-byte load
 #pragma unroll
             for (int m = 0; m < 16; m += 2) {
@@ -400,6 +443,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
     // ---------------- epilogue ----------------
     const int w4 = warp - 4;
     const uint32_t lane_base = static_cast<uint32_t>(w4 * 32) << 16;
+    const bool odd = lane & 1;
     uint32_t sbase = static_cast<uint32_t>(w4 * 32 + lane);
 #pragma unroll
     for (int b = 0; b < K; ++b) {
@@ -409,7 +453,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
     uint32_t iter = 0;
     for (uint64_t tile = blockIdx.x; tile < a.num_tiles; tile += gridDim.x, ++iter) {
       const uint32_t db = iter & 1;
-      if (!mbar_wait(&d_full[db], (iter >> 1) & 1, a.err, 2)) break;
+      if (!warp_ok<MODE == kSetPairs>(mbar_wait(&d_full[db], (iter >> 1) & 1, a.err, 2))) break;
       fence_after();
       uint64_t base = tile << a.C;
       for (int j = 0; j < a.nh; ++j) {
@@ -426,7 +470,20 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           if (cb + h >= N / 32) break;
-          if constexpr (PAIR) {
+          if constexpr (MODE == kSetPairs) {
+#pragma unroll
+            for (int j = 0; j < 16; j += 2) {
+              const int i = (cb + h) * 16 + j;
+              const float2 mj = make_float2(__uint_as_float(v[h][2 * j]), __uint_as_float(v[h][2 * j + 1]));
+              const float2 mj1 = make_float2(__uint_as_float(v[h][2 * j + 2]), __uint_as_float(v[h][2 * j + 3]));
+              // the even thread writes member j of both sets, the odd one member j + 1
+              const float rx = __shfl_xor_sync(0xffffffffu, odd ? mj.x : mj1.x, 1);
+              const float ry = __shfl_xor_sync(0xffffffffu, odd ? mj.y : mj1.y, 1);
+              const uint32_t l = (sbase & ~1u) | (odd ? a.moff[i + 1] : a.moff[i]);
+              __stcs(reinterpret_cast<float4*>(psi + (base | a.roff[l >> a.C] | (l & rowmask))),
+                     odd ? make_float4(rx, ry, mj1.x, mj1.y) : make_float4(mj.x, mj.y, rx, ry));
+            }
+          } else if constexpr (MODE == kMemberPairs) {
 #pragma unroll
             for (int j = 0; j < 16; j += 2) {
               const uint32_t l = sbase | a.moff[(cb + h) * 16 + j];
@@ -501,6 +558,18 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
   }
 }
 
+// Set pairs pay where a warp's 8-byte accesses conflict 8-way or worse: a
+// 128-byte line of banks holds 16 amplitudes, so a half-warp's sets spread
+// over 2^(non-targets among amplitude bits 0..3) bank offsets, which is 2
+// when bits 1, 2 and 3 are all targets.  With 4-way conflicts or fewer the
+// extra shuffles cost more than the wavefronts they save (measured).
+template <int K>
+static bool low_targets(const uint32_t* targets) {
+  int low = 0;
+  for (int b = 0; b < K; ++b) low += targets[b] >= 1u && targets[b] <= 3u;
+  return low == 3;
+}
+
 template <int K>
 static cudaError_t launch_tc_k(float2* psi, int n, const uint32_t* targets, const float* wdev, int* err,
                                cudaStream_t st, uint32_t lbo_override, uint32_t sbo_override) {
@@ -512,10 +581,13 @@ static cudaError_t launch_tc_k(float2* psi, int n, const uint32_t* targets, cons
   const size_t smem = 2 * sizeof(float) * N * N + TBUF_AMPS * sizeof(float2) + 24 * sizeof(uint64_t) + 16;
   static PerDevice attr_set;
   const cudaError_t attr_err = static_cast<cudaError_t>(attr_set.get([&] {
-    cudaError_t e = cudaFuncSetAttribute(k_apply_tc<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_apply_tc<K, kSingle>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_apply_tc<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(k_apply_tc<K, kMemberPairs>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               static_cast<int>(smem));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_apply_tc<K, kSetPairs>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                static_cast<int>(smem));
     return static_cast<int>(e);
   }));
@@ -560,9 +632,11 @@ static cudaError_t launch_tc_k(float2* psi, int n, const uint32_t* targets, cons
   uint64_t grid = static_cast<uint64_t>(sm_count());
   if (grid > a.num_tiles) grid = a.num_tiles;
   if (a.moff[1] == 1u)            // qubit 0 is a target (targets ascending)
-    k_apply_tc<K, true><<<static_cast<unsigned>(grid), tc::kThreads, smem, st>>>(psi, a);
+    k_apply_tc<K, kMemberPairs><<<static_cast<unsigned>(grid), tc::kThreads, smem, st>>>(psi, a);
+  else if (low_targets<K>(targets))
+    k_apply_tc<K, kSetPairs><<<static_cast<unsigned>(grid), tc::kThreads, smem, st>>>(psi, a);
   else
-    k_apply_tc<K, false><<<static_cast<unsigned>(grid), tc::kThreads, smem, st>>>(psi, a);
+    k_apply_tc<K, kSingle><<<static_cast<unsigned>(grid), tc::kThreads, smem, st>>>(psi, a);
   return cudaGetLastError();
 }
 

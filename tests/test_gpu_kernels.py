@@ -101,6 +101,7 @@ LOW_RUN_PATTERNS = [
     [0, 1, 2, 3, 4, 5], [0, 1, 6, 7, 8, 9], [1, 2, 3, 9, 10, 11], [3, 4, 5, 11, 12, 13],
     [0, 1, 8, 9, 16, 17], [1, 2, 3, 4, 10, 11], [1, 2, 9, 10, 17, 18], [0, 1, 2, 3, 8, 9],
     [0, 1, 2, 3], [0, 1, 8, 9], [1, 2, 9, 10], [0, 1, 2, 3, 4], [0, 1, 2, 8, 9], [1, 2, 3, 9, 10],
+    [1, 2, 3, 9], [1, 2, 3, 5, 16], [1, 2, 3, 4, 5, 6], [2, 3, 9, 10, 17, 18],
 ]
 
 
@@ -108,7 +109,9 @@ def test_apply_tf32x3_low_target_runs(qt, orc):
     """Target patterns whose gather sets are aligned runs of low amplitudes (the
     6-qubit gates of the 32-qubit precision workload whose converter reads conflict
     in shared memory, and 4- and 5-qubit analogues), with and without high targets,
-    against the oracle."""
+    against the oracle.  Covers the three ways the kernel moves amplitudes: member
+    pairs (qubit 0 a target), set pairs exchanged by shuffles (qubits 1, 2 and 3
+    targets, qubit 0 not) and single members."""
     n = 20
     rng = np.random.default_rng(77)
     for qubits in LOW_RUN_PATTERNS:
