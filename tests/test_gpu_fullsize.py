@@ -14,13 +14,18 @@ any size:
     record equals the decision the oracle's own Philox draws and lower
     bounds give; flushes happen exactly where stage 1 cannot decide; as a
     consistency check of two different kernels, the sampled bitstrings'
-    per-qubit frequencies agree with <Z_j> of the same final states.
+    per-qubit frequencies agree with <Z_j> of the same final states;
+  * opt-in (QT_FULL_ORACLE=1, about ten minutes of FP64 on the host cores):
+    one whole trajectory of that workload, oracle against library.
 """
+import os
+import time
+
 import numpy as np
 import pytest
 
 import qtsynth as qs
-from gpu_util import KERNEL_L2, STATE_L2, torch_cuda
+from gpu_util import KERNEL_L2, MARGIN, STATE_FID, STATE_L2, torch_cuda
 
 pytestmark = pytest.mark.gpu
 N = 30
@@ -170,3 +175,82 @@ def test_grid30_branch_records_and_marginals(qt, orc):
         se = np.sqrt(np.maximum(p1 * (1 - p1), 1e-4) / S)
         assert np.all(np.abs(bits.mean(0) - p1) < 5 * se)
     assert lbs  # lower bounds were evaluated by the oracle
+
+
+def _chunked_l2_fidelity(g, ref, chunk=1 << 26):
+    """Relative L2 distance and fidelity of complex64 g against complex128 ref,
+    a slice at a time (2^30 amplitudes do not fit comfortably in temporaries)."""
+    diff = nref = ng = 0.0
+    dot = 0j
+    for i in range(0, ref.size, chunk):
+        a = g[i:i + chunk].astype(np.complex128)
+        b = ref[i:i + chunk]
+        diff += float(np.sum(np.abs(a - b) ** 2))
+        nref += float(np.sum(np.abs(b) ** 2))
+        ng += float(np.sum(np.abs(a) ** 2))
+        dot += np.vdot(b, a)
+    return float(np.sqrt(diff / nref)), float(abs(dot) ** 2 / (ng * nref))
+
+
+@pytest.mark.skipif(os.environ.get("QT_FULL_ORACLE") != "1",
+                    reason="one whole 30-qubit FP64 oracle trajectory takes about ten minutes "
+                           "(QT_FULL_ORACLE=1 runs it)")
+def test_grid30_full_trajectory_against_oracle(qt, orc):
+    """Trajectory 0 of the 30-qubit grid workload end to end: the FP64 oracle's
+    whole unfused trajectory against the library's plain loop in the benchmark's
+    configuration (fused k = 4, delayed inner products, 100 samples).  Every
+    branch record where the oracle's margin exceeds 1e-6, the final state
+    (relative L2, fidelity), the samples where the CDF margin exceeds 1e-6 and,
+    for the others, the oracle's CDF neighbourhood of their targets.
+    Prints the oracle's wall time for the whole trajectory, the figure that the
+    benchmark's CPU baseline extrapolates from a prefix of the ops."""
+    circ = qs.config1_circuit()
+    f = qt.Fused(qt.Circuit.from_synth(circ), 4)
+    S = 100
+    run = qt.Run(f, 1, seed=0, first_traj=0, samples_per_traj=S, keep_states=True)
+    kr, st = run.kraus_indices()
+    smp = run.samples()[0]
+    g = run.state(0)
+    del run
+    t0 = time.perf_counter()
+    ref = orc.run_trajectory(circ, orc.DELAYED, seed=0, traj=0)
+    t_traj = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    want, margin = orc.sample(ref["state"], 0, 0, S)
+    t_smp = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0))
+    print(f"\noracle, whole trajectory 0 of the 30-qubit grid workload ({len(circ.ops)} ops): "
+          f"{t_traj:.1f} s + {S} samples {t_smp:.1f} s on {cores} cores = "
+          f"{1.0 / (t_traj + t_smp):.6f} trajectories/s")
+    # records up to the first tie (after a tie the two may take different branches)
+    ties = np.flatnonzero(ref["margin"] <= MARGIN)
+    first = int(ties[0]) if ties.size else ref["margin"].size
+    assert np.array_equal(kr[0][:first], ref["kraus_idx"][:first])
+    assert np.array_equal(st[0][:first], ref["stage"][:first])
+    if ties.size:
+        pytest.skip(f"branch tie at channel {first}: records compared up to it")
+    l2, fid = _chunked_l2_fidelity(g, ref["state"])
+    print(f"branch records compared: {first} (stage 2: {int((ref['stage'] == 2).sum())}); "
+          f"state relative L2 {l2:.3e}, fidelity 1 - {1 - fid:.2e}; "
+          f"samples compared: {int((margin > MARGIN).sum())} of {S}")
+    assert l2 <= STATE_L2 and fid >= 1 - STATE_FID
+    np.testing.assert_array_equal(smp[margin > MARGIN], want[margin > MARGIN])
+    # At 2^30 amplitudes each probability is ~1e-9, so nearly every sample is a
+    # tie by the 1e-6 margin.  Those must lie in the oracle's CDF neighbourhood
+    # of their target u * C(2^n - 1): [C(x - 1) - delta, C(x) + delta].  delta
+    # bounds |C_gpu - C_oracle|: the sampler's own rounding (FP32 squares, runs
+    # of at most 1024 terms, FP64 across runs: 32 * 2^-24, as the sampler tests
+    # check) plus the state difference, sum_y ||g_y|^2 - |r_y|^2| <= l2 (2 + l2).
+    tie = margin <= MARGIN
+    if tie.any():
+        co = np.cumsum(np.abs(ref["state"]) ** 2)
+        delta = 32 * 2.0 ** -24 * co[-1] + l2 * (2 + l2) * co[-1]
+        u = np.array([orc.u01(0, 0, 1, j) for j in range(S)])
+        t = u[tie] * co[-1]
+        x = smp[tie].astype(np.int64)
+        below = np.where(x > 0, co[np.maximum(x - 1, 0)], 0.0)
+        print(f"ties checked against the oracle's CDF neighbourhood: {int(tie.sum())} (delta {delta:.2e}); "
+              f"largest distance of a target outside its sample's CDF interval: "
+              f"{float(max(np.max(below - t), np.max(t - co[x]), 0.0)):.2e}")
+        assert np.all(t >= below - delta), np.min(t - below + delta)
+        assert np.all(t <= co[x] + delta), np.min(co[x] + delta - t)
