@@ -385,48 +385,50 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
           tb = tbuf + rs * (TILE_AMPS / 2);
           tsub = static_cast<uint32_t>(c) * (TILE_AMPS / 2);
         }
+        // this chunk's members of the thread's set, read from the staged tile
+        // before waiting for the TMEM slot (the reads do not depend on it)
+        float2 val[MPC];
+        if constexpr (MODE == kSetPairs) {
+#pragma unroll
+          for (int m = 0; m < MPC; m += 2) {
+            const int i = c * MPC + m;
+            const uint32_t mo = odd ? a.moff[i + 1] : a.moff[i];
+            const float4 v = *reinterpret_cast<const float4*>(tb + (((sbase & ~1u) | mo) - tsub));
+            // even: (x, y) is its member m, (z, w) the odd thread's member m;
+            // odd: (z, w) is its member m + 1, (x, y) the even thread's
+            const float rx = __shfl_xor_sync(0xffffffffu, odd ? v.x : v.z, 1);
+            const float ry = __shfl_xor_sync(0xffffffffu, odd ? v.y : v.w, 1);
+            val[m] = odd ? make_float2(rx, ry) : make_float2(v.x, v.y);
+            val[m + 1] = odd ? make_float2(v.z, v.w) : make_float2(rx, ry);
+          }
+        } else if constexpr (MODE == kMemberPairs) {
+          // members 2j and 2j + 1 are adjacent amplitudes: one 16-byte load
+#pragma unroll
+          for (int m = 0; m < MPC; m += 2) {
+            const float4 v = *reinterpret_cast<const float4*>(tb + ((sbase | a.moff[c * MPC + m]) - tsub));
+            val[m] = make_float2(v.x, v.y);
+            val[m + 1] = make_float2(v.z, v.w);
+          }
+        } else {
+#pragma unroll
+          for (int m = 0; m < MPC; ++m) val[m] = tb[(sbase | a.moff[c * MPC + m]) - tsub];
+        }
+        // the staged bytes are in registers: hand the buffer back to the producer
+        if (split) mbar_arrive(&t_empty[rs]);                       // this chunk half
+        else if (c == NCHUNK - 1) mbar_arrive(&t_empty[b]);         // the tile's last chunk
         const uint32_t slot = chunk_iter & 1;
         const uint32_t use = chunk_iter >> 1;
         if (use > 0 && !warp_ok<MODE == kSetPairs>(mbar_wait(&a_empty[slot], (use - 1) & 1, a.err, 1))) {
           ok = false;
           break;
         }
-        uint32_t hi[32], lo[32];
 #pragma unroll
         for (int half = 0; half < MPC / 16; ++half) {
-          if constexpr (MODE == kSetPairs) {
+          uint32_t hi[32], lo[32];
 #pragma unroll
-            for (int m = 0; m < 16; m += 2) {
-              const int i = c * MPC + half * 16 + m;
-              const uint32_t mo = odd ? a.moff[i + 1] : a.moff[i];
-              const float4 v = *reinterpret_cast<const float4*>(tb + (((sbase & ~1u) | mo) - tsub));
-              // even: (x, y) is its member m, (z, w) the odd thread's member m;
-              // odd: (z, w) is its member m + 1, (x, y) the even thread's
-              const float rx = __shfl_xor_sync(0xffffffffu, odd ? v.x : v.z, 1);
-              const float ry = __shfl_xor_sync(0xffffffffu, odd ? v.y : v.w, 1);
-              split_tf32(odd ? rx : v.x, hi[2 * m], lo[2 * m]);
-              split_tf32(odd ? ry : v.y, hi[2 * m + 1], lo[2 * m + 1]);
-              split_tf32(odd ? v.z : rx, hi[2 * m + 2], lo[2 * m + 2]);
-              split_tf32(odd ? v.w : ry, hi[2 * m + 3], lo[2 * m + 3]);
-            }
-          } else if constexpr (MODE == kMemberPairs) {
-            // members 2j and 2j + 1 are adjacent amplitudes: one 16-byte load
-#pragma unroll
-            for (int m = 0; m < 16; m += 2) {
-              const float4 v =
-                  *reinterpret_cast<const float4*>(tb + ((sbase | a.moff[c * MPC + half * 16 + m]) - tsub));
-              split_tf32(v.x, hi[2 * m], lo[2 * m]);
-              split_tf32(v.y, hi[2 * m + 1], lo[2 * m + 1]);
-              split_tf32(v.z, hi[2 * m + 2], lo[2 * m + 2]);
-              split_tf32(v.w, hi[2 * m + 3], lo[2 * m + 3]);
-            }
-          } else {
-#pragma unroll
-            for (int m = 0; m < 16; ++m) {
-              const float2 v = tb[(sbase | a.moff[c * MPC + half * 16 + m]) - tsub];
-              split_tf32(v.x, hi[2 * m], lo[2 * m]);
-              split_tf32(v.y, hi[2 * m + 1], lo[2 * m + 1]);
-            }
+          for (int m = 0; m < 16; ++m) {
+            split_tf32(val[half * 16 + m].x, hi[2 * m], lo[2 * m]);
+            split_tf32(val[half * 16 + m].y, hi[2 * m + 1], lo[2 * m + 1]);
           }
           const uint32_t col = a_col0 + slot * 128 + half * 32;
           tmem_st32(tmem + lane_base + col, hi);
@@ -435,9 +437,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
         tmem_wait_st();
         fence_before();
         mbar_arrive(&a_full[slot]);
-        if (split) mbar_arrive(&t_empty[rs]);  // done reading this chunk half
       }
-      if (!split && ok) mbar_arrive(&t_empty[b]);   // done reading the staged tile
     }
   } else if (warp < 8) {
     // ---------------- epilogue ----------------
