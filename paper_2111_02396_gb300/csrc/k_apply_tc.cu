@@ -22,13 +22,18 @@
 //              buffers for k = 4, 4 for k = 5, and for k = 6 (B takes 128 KB)
 //              one buffer staged as two chunk halves;
 //   warps 0-3  converters: thread t owns set t of the tile (TMEM lane t); it
-//              reads its members from the staged tile, splits hi/lo, and
-//              writes A to TMEM with tcgen05.st (A operand taken from TMEM);
+//              reads a chunk of its members from the staged tile into
+//              registers, hands the staged bytes back to the producer, waits
+//              for its TMEM slot, splits hi/lo, and writes A to TMEM with
+//              tcgen05.st (A operand taken from TMEM);
 //   warp 8     MMA issuer: one elected thread issues tcgen05.mma (M=128,
 //              N=2^(k+1), K=8 per instruction) with A in TMEM and B in
 //              shared memory, and commits to mbarriers;
 //   warps 4-7  epilogue: tcgen05.ld of the accumulator rows, stores of the
 //              output sets (consecutive threads, consecutive sets).
+// How the converters and the epilogue address amplitudes (single 8-byte
+// members, 16-byte member pairs, or 16-byte set pairs exchanged by shuffles)
+// is a template parameter chosen per target pattern (see MODE below).
 // TMEM (512 columns): two A slots of 128 columns (hi at +0, lo at +64; one
 // chunk of up to 32 members) and two accumulators of N columns (at 256 and
 // 256 + N), so conversion, MMA and draining overlap while the next tile's
@@ -564,7 +569,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
 // when bits 1, 2 and 3 are all targets.  With 4-way conflicts or fewer the
 // extra shuffles cost more than the wavefronts they save (measured).
 template <int K>
-static bool low_targets(const uint32_t* targets) {
+static bool set_pairs_pay(const uint32_t* targets) {
   int low = 0;
   for (int b = 0; b < K; ++b) low += targets[b] >= 1u && targets[b] <= 3u;
   return low == 3;
@@ -633,7 +638,7 @@ static cudaError_t launch_tc_k(float2* psi, int n, const uint32_t* targets, cons
   if (grid > a.num_tiles) grid = a.num_tiles;
   if (a.moff[1] == 1u)            // qubit 0 is a target (targets ascending)
     k_apply_tc<K, kMemberPairs><<<static_cast<unsigned>(grid), tc::kThreads, smem, st>>>(psi, a);
-  else if (low_targets<K>(targets))
+  else if (set_pairs_pay<K>(targets))
     k_apply_tc<K, kSetPairs><<<static_cast<unsigned>(grid), tc::kThreads, smem, st>>>(psi, a);
   else
     k_apply_tc<K, kSingle><<<static_cast<unsigned>(grid), tc::kThreads, smem, st>>>(psi, a);
