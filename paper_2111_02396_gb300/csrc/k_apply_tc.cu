@@ -377,6 +377,9 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
       const uint32_t b = split ? 0u : it % NBUF;
       if (!split && !warp_ok<MODE == kSetPairs>(mbar_wait(&t_full[b], (it / NBUF) & 1, a.err, 64))) break;
       const float2* tb = tbuf + b * TILE_AMPS;
+      // chunk and column-block loops stay rolled: four roles of one CTA run
+      // different code, and the smaller kernel measured faster
+#pragma unroll 1
       for (int c = 0; c < NCHUNK; ++c, ++chunk_iter) {
         // split: this chunk half sits in ring slot chunk_iter % RING; its members'
         // tile offsets carry the top target bit (TILE_AMPS / 2) when c = 1
@@ -466,7 +469,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_apply_tc(float2* __restrict
         base = ((base >> h) << (h + 1)) | (base & ((1ull << h) - 1ull));
       }
       // accumulator columns in blocks of 32, two loads in flight per wait
-#pragma unroll
+#pragma unroll 1
       for (int cb = 0; cb < N / 32; cb += 2) {
         uint32_t v[2][32];
         tmem_ld32(tmem + lane_base + d_col0 + db * N + cb * 32, v[0]);
