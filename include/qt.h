@@ -200,6 +200,8 @@ typedef struct {
   uint64_t prefix_copies;     /* QT_FLAG_SHARE_PREFIX: copies of the shared state */
   uint64_t prefix_ops;        /* QT_FLAG_SHARE_PREFIX: operations the trajectories took from the
                                  shared state (summed over trajectories) */
+  uint64_t merged_pieces;     /* segment pieces merged into a later piece on the same qubits
+                                 (at most the fusion width together); not in fused_passes */
 } qt_run_stats_t;
 qt_status qt_run_stats(const qt_run* r, qt_run_stats_t* out);
 

@@ -473,7 +473,66 @@ struct Controller {
   // pieces (moved earlier past pieces they share no qubit with) whose qubits
   // lie in {0..6} plus at most kGroupMaxHigh higher qubits share one
   // multi-gate pass over the state.
-  qt_status launch_pieces(float2* psi, const std::vector<Piece>& pieces) {
+  // Peephole merge of a segment's pieces, extending the fusion of Sec. III.B
+  // across the cuts that flush points make: a piece moves forward to the
+  // first later piece that shares a qubit with it (every piece in between
+  // acts on other qubits, so the two commute) and the two become one piece
+  // when their qubits number at most the run's fusion width.  A flush point
+  // cuts the fused gates in flight into before- and after-pieces; merged with
+  // a neighbour, such a remainder costs no pass of its own.  The product is
+  // formed in FP64 from the pieces' FP32 matrices and rounded once.
+  std::vector<cd> mtmp, mcol;
+  void merge_pieces(std::vector<Piece>& pieces) {
+    const int kmax = static_cast<int>(f.kmax);
+    std::vector<char> gone(pieces.size(), 0);
+    size_t merged = 0;
+    for (size_t a = 0; a < pieces.size(); ++a) {
+      if (gone[a]) continue;
+      size_t b = a + 1;
+      while (b < pieces.size() && (gone[b] || !(pieces[b].full & pieces[a].full))) ++b;
+      if (b == pieces.size()) continue;
+      const uint64_t u = pieces[a].full | pieces[b].full;
+      if (std::popcount(u) > kmax) continue;
+      std::vector<uint32_t> targets;
+      for (uint32_t q = 0; q < 64; ++q)
+        if (u & (1ull << q)) targets.push_back(q);
+      const int w = static_cast<int>(targets.size()), D = 1 << w;
+      // columns of the identity, then piece a, then piece b (column-major)
+      mcol.assign(static_cast<size_t>(D) * D, cd(0.0));
+      for (int j = 0; j < D; ++j) mcol[static_cast<size_t>(j) * D + j] = 1.0;
+      for (const Piece* P : {&pieces[a], &pieces[b]}) {
+        const int q = static_cast<int>(P->targets.size()), d = 1 << q;
+        int pos[QT_MAX_OP_QUBITS];
+        for (int i = 0; i < q; ++i)
+          pos[i] = static_cast<int>(std::lower_bound(targets.begin(), targets.end(), P->targets[i]) - targets.begin());
+        mtmp.resize(static_cast<size_t>(d) * d);
+        for (int i = 0; i < d * d; ++i) mtmp[i] = cd(P->u[i].x, P->u[i].y);
+        for (int j = 0; j < D; ++j) apply_small(&mcol[static_cast<size_t>(j) * D], w, q, pos, mtmp.data());
+      }
+      owned.emplace_back(static_cast<size_t>(D) * D);
+      std::vector<float2>& M = owned.back();
+      for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) {
+          const cd x = mcol[static_cast<size_t>(j) * D + i];
+          M[static_cast<size_t>(i) * D + j] = make_float2(static_cast<float>(x.real()), static_cast<float>(x.imag()));
+        }
+      pieces[b] = Piece{std::move(targets), M.data(), u};
+      gone[a] = 1;
+      ++merged;
+    }
+    if (!merged) return;
+    size_t o = 0;
+    for (size_t i = 0; i < pieces.size(); ++i) {
+      if (gone[i]) continue;
+      if (o != i) pieces[o] = std::move(pieces[i]);   // never onto itself (that empties a vector)
+      ++o;
+    }
+    pieces.resize(o);
+    R.stats.merged_pieces += merged;
+  }
+
+  qt_status launch_pieces(float2* psi, std::vector<Piece>& pieces) {
+    merge_pieces(pieces);
     const bool group = (R.p.flags & QT_FLAG_MULTI_GATE) && R.n >= 8;
     const int hmax = std::min<int>(kGroupMaxHigh, static_cast<int>(R.n) - 7);
     const uint64_t low = (1ull << 7) - 1ull;

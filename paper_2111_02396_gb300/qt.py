@@ -60,7 +60,7 @@ class qt_run_stats_t(C.Structure):
                 ("kernel_launches", C.c_uint64), ("fused_pieces", C.c_uint64),
                 ("passes_by_width", C.c_uint64 * 8), ("apply_ms_by_width", C.c_double * 8),
                 ("folded_pieces", C.c_uint64), ("fold_split", C.c_uint32), ("pad", C.c_uint32),
-                ("prefix_copies", C.c_uint64), ("prefix_ops", C.c_uint64)]
+                ("prefix_copies", C.c_uint64), ("prefix_ops", C.c_uint64), ("merged_pieces", C.c_uint64)]
 
 
 class qt_fused_info_t(C.Structure):
