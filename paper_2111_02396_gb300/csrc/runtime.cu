@@ -483,7 +483,8 @@ struct Controller {
   // formed in FP64 from the pieces' FP32 matrices and rounded once.
   std::vector<cd> mtmp, mcol;
   void merge_pieces(std::vector<Piece>& pieces) {
-    const int kmax = static_cast<int>(f.kmax);
+    // 6-qubit passes need n >= 13 (the run checks its fused gates for that up front)
+    const int kmax = std::min(static_cast<int>(f.kmax), R.n >= 13 ? 6 : 5);
     std::vector<char> gone(pieces.size(), 0);
     size_t merged = 0;
     for (size_t a = 0; a < pieces.size(); ++a) {
